@@ -1,0 +1,368 @@
+#!/usr/bin/env python
+"""Benchmark of the sorption moment-propagation hot path on one GB300 (or N replicas).
+
+Workload (one "step" = one whole job, every stage of the path on one medium):
+  random porous medium 128^3, overlapping solid spheres of radius 6, porosity 0.40, seed 1
+  (periodic), uniform body force along x set once so that the mean fluid velocity is 0.01;
+    1. geometry prep on the device (node classes, interface bits and offsets),
+    2. lb_steady: BGK tau = 1 from rest until max|u(t) - u(t-1)| < 1e-7 (checked every 100),
+    3. mp_init: one species, D_b = 0.05, k_a = k_d = 5e-3, FP32 storage, FP64 reductions,
+    4. mp_step: 2e4 moment-propagation + sorption steps with Z(t) and D(t) on the device.
+Metric: moment-propagation node-species updates per second of the whole job (fluid nodes
+x species x MP steps / job time). The LB steps to steady state are reported beside it.
+`value` is timed with CUDA events on the launching stream with the medium already on the
+device; `e2e` times the same job from a host solid mask to host Z(t)/D(t) arrays.
+
+python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
+Under torchrun each rank runs an independent replica (no data exchange: the path has none
+across jobs); value = all ranks' updates / the slowest rank's time.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+WORKLOAD = {
+    "workload": "random-sphere porous medium 128^3 (R=6, porosity 0.40, seed 1): LB to steady + "
+                "2e4 sorption-MP steps, 1 species",
+    "lattice": [128, 128, 128],
+    "radius": 6,
+    "porosity": 0.40,
+    "seed": 1,
+    "mean_u": 0.01,
+    "tau": 1.0,
+    "lb_tol": 1e-7,
+    "lb_check_every": 100,
+    "D_b": 0.05,
+    "k_a": 5e-3,
+    "k_d": 5e-3,
+    "species": 1,
+    "mp_steps": 20000,
+    "precision": "fp32 storage and arithmetic, fp64 reductions and D(t)",
+}
+# LB steps to steady state of this workload, measured by the GPU arm (cold start); used only
+# to scale the oracle's per-step CPU times to a whole job in the reference arm.
+LB_STEPS_ASSUMED = 4000
+
+METRIC = "sorption-MP node-species updates/s (whole job incl. LB to steady)"
+UNIT = "node-species updates/s"
+
+# DRAM traffic per launch from ncu (dram__bytes_read.sum + dram__bytes_write.sum), valid only
+# while the kernel source hashes to `src_sha`; otherwise reported as null.
+TRAFFIC = {}
+
+
+def _src_sha(name):
+    p = os.path.join(ROOT, "paper_1303_2470_gb300", "csrc", name)
+    return hashlib.sha256(open(p, "rb").read()).hexdigest()[:16]
+
+
+def _peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        d = json.load(open(p))
+        return float(d["hbm_gbs"]), "measured"
+    return 6800.0, "fallback"
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled every 200 ms while running."""
+
+    QUERY = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+             "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+             "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.proc = None
+        self.path = None
+
+    def start(self):
+        try:
+            fd, self.path = tempfile.mkstemp(suffix=".csv")
+            os.close(fd)
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.QUERY}",
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+        except OSError:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        rows = []
+        for line in open(self.path):
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                rows.append((float(parts[1]), float(parts[2]), parts[5:9]))
+            except ValueError:
+                continue
+        os.unlink(self.path)
+        if not rows:
+            return None
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({n for _, _, flags in rows for n, f in zip(names, flags) if f == "Active"})
+        loaded = [r[0] for r in rows]
+        return {"sm_mhz": statistics.median(loaded), "sm_max_mhz": max(r[1] for r in rows),
+                "reasons": reasons, "samples": len(rows)}
+
+
+def make_medium():
+    from paper_1303_2470_gb300 import media
+    nz, ny, nx = WORKLOAD["lattice"][::-1]
+    solid, nspheres = media.random_spheres((nz, ny, nx), WORKLOAD["radius"], WORKLOAD["porosity"],
+                                           WORKLOAD["seed"])
+    return solid, nspheres
+
+
+# ----------------------------------------------------------------------------------------
+# oracle sample (CPU baseline and the reference arm)
+# ----------------------------------------------------------------------------------------
+def oracle_sample(solid, lb_steps_job, lb_sample=5, mp_sample=15):
+    """Times the FP64 oracle as it stands on a bounded sample of the workload and scales
+    it to one job: LB per-step time x lb_steps_job + MP setup + per-step time x 2e4."""
+    import oracle
+    oracle.build()
+    F = (1e-5, 0.0, 0.0)
+    f = oracle.lb_init(solid)
+    t0 = time.perf_counter()
+    for _ in range(lb_sample):
+        f, u = oracle.lb_step(solid, f, F, WORKLOAD["tau"])
+    t_lb = (time.perf_counter() - t0) / lb_sample
+    p = oracle.Problem(solid, u, WORKLOAD["D_b"], WORKLOAD["k_a"], WORKLOAD["k_d"])
+    t0 = time.perf_counter()
+    oracle.run(p, g=0, nsteps=0)
+    t_setup = time.perf_counter() - t0
+    t0 = time.perf_counter()
+    oracle.run(p, g=0, nsteps=mp_sample)
+    t_mp = max(time.perf_counter() - t0 - t_setup, 1e-9) / mp_sample
+    n_fluid = int((solid == 0).sum())
+    job_s = t_lb * lb_steps_job + t_setup + t_mp * WORKLOAD["mp_steps"]
+    value = n_fluid * WORKLOAD["species"] * WORKLOAD["mp_steps"] / job_s
+    cores = int(os.environ.get("OMP_NUM_THREADS", os.cpu_count() or 1))
+    sample = (f"oracle (FP64 C, OpenMP) on the same 128^3 medium: {lb_sample} LB steps "
+              f"({t_lb*1e3:.0f} ms/step) and {mp_sample} MP steps ({t_mp*1e3:.0f} ms/step, setup "
+              f"{t_setup:.1f} s), scaled to {lb_steps_job} LB steps + {WORKLOAD['mp_steps']} MP steps")
+    return {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle", "sample": sample,
+            "job_s_estimate": job_s}
+
+
+def run_reference(args):
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return 0
+    solid, _ = make_medium()
+    for _ in range(args.warmup):
+        oracle_sample(solid, LB_STEPS_ASSUMED, lb_sample=2, mp_sample=3)
+    vals = []
+    for _ in range(args.steps):
+        vals.append(oracle_sample(solid, LB_STEPS_ASSUMED))
+    value = statistics.median(v["value"] for v in vals)
+    job_ms = statistics.median(v["job_s_estimate"] for v in vals) * 1e3
+    cfg = dict(WORKLOAD)
+    cfg["l2"] = "n/a (host)"
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": job_ms,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic", "config": cfg,
+            "cpu_baseline": {k: vals[-1][k] for k in ("kind", "cores", "sample")} | {"value": value,
+                                                                                    "unit": UNIT},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line))
+    return 0
+
+
+# ----------------------------------------------------------------------------------------
+# GPU arm
+# ----------------------------------------------------------------------------------------
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--mp-steps", type=int, default=WORKLOAD["mp_steps"])
+    args = ap.parse_args()
+    WORKLOAD["mp_steps"] = args.mp_steps
+    if args.impl == "reference":
+        return run_reference(args)
+
+    import torch
+    import torch.distributed as dist
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if world > 1:
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl")
+    else:
+        torch.cuda.set_device(0)
+    dev = torch.device("cuda", torch.cuda.current_device())
+
+    from paper_1303_2470_gb300 import build
+    build.build()
+    from paper_1303_2470_gb300 import mp
+
+    solid, nspheres = make_medium()
+    n_fluid = int((solid == 0).sum())
+    solid_dev = torch.as_tensor(solid).to(dev)
+    stream = torch.cuda.current_stream(dev)
+    u = torch.zeros((3,) + solid.shape, dtype=torch.float32, device=dev)
+
+    # force set once (Stokes-linear): mean fluid u_x = 0.01
+    F0 = 1e-5
+    mp.lb_steady(solid_dev, (F0, 0, 0), u, tau=WORKLOAD["tau"], tol=WORKLOAD["lb_tol"],
+                 max_steps=200_000, check_every=WORKLOAD["lb_check_every"], stream=stream)
+    mean0 = float(u[0][solid_dev == 0].double().mean())
+    Fx = F0 * WORKLOAD["mean_u"] / mean0
+    force = (Fx, 0.0, 0.0)
+    flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device=dev)  # 256 MiB > L2
+
+    def job(solid_arg, host_out=None):
+        """One pass of the whole path. Returns (lb_steps, ctx info, event list)."""
+        ev = [torch.cuda.Event(enable_timing=True) for _ in range(4)]
+        ev[0].record(stream)
+        steps, res, conv = mp.lb_steady(solid_arg, force, u, tau=WORKLOAD["tau"], tol=WORKLOAD["lb_tol"],
+                                        max_steps=200_000, check_every=WORKLOAD["lb_check_every"],
+                                        stream=stream)
+        ev[1].record(stream)
+        ctx = mp.mp_init(solid_arg, u, WORKLOAD["D_b"], WORKLOAD["k_a"], WORKLOAD["k_d"],
+                         capacity=WORKLOAD["mp_steps"] + 2, stream=stream)
+        ev[2].record(stream)
+        mp.mp_step(ctx, WORKLOAD["mp_steps"])
+        if host_out is not None:
+            mp.mp_vacf_into(ctx, 0, 0, host_out[0], host_out[1])
+        ev[3].record(stream)
+        info = mp.mp_info(ctx)
+        return steps, res, conv, info, ev, ctx
+
+    for _ in range(args.warmup):
+        *_, ctx = job(solid_dev)
+        torch.cuda.synchronize()
+        ctx.close()
+
+    clocks = ClockSampler(dev.index)
+    clocks.start()
+    if world > 1:
+        dist.barrier()
+    torch.cuda.synchronize()
+    total_ms, lb_ms, init_ms, mp_ms, lb_steps_all, launches = 0.0, 0.0, 0.0, 0.0, [], 0
+    info = None
+    for _ in range(args.steps):
+        flush.fill_(1.0)  # evict the previous job's data from L2 (outside the timed events)
+        steps, res, conv, info, ev, ctx = job(solid_dev)
+        torch.cuda.synchronize()
+        total_ms += ev[0].elapsed_time(ev[3])
+        lb_ms += ev[0].elapsed_time(ev[1])
+        init_ms += ev[1].elapsed_time(ev[2])
+        mp_ms += ev[2].elapsed_time(ev[3])
+        lb_steps_all.append(steps)
+        # kernels: LB (2 geometry + init + steps), MP (3 geometry + convert + negative check
+        # + init + steps)
+        launches += 3 + steps + 6 + WORKLOAD["mp_steps"]
+        ctx.close()
+    torch.cuda.synchronize()
+    if world > 1:
+        dist.barrier()
+    clk = clocks.stop()
+    t = torch.tensor([total_ms], dtype=torch.float64, device=dev)
+    if world > 1:
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    total_ms_max = float(t.item())
+    units_per_job = n_fluid * WORKLOAD["species"] * WORKLOAD["mp_steps"]
+    value = units_per_job * args.steps * world / (total_ms_max / 1e3)
+
+    # end to end through the public API: host solid mask in, host Z(t)/D(t) out
+    Zh = torch.empty(WORKLOAD["mp_steps"] + 2, dtype=torch.float64, pin_memory=True).numpy()
+    Dh = torch.empty(WORKLOAD["mp_steps"] + 2, dtype=torch.float64, pin_memory=True).numpy()
+    e2e_s = 0.0
+    for _ in range(args.steps):
+        flush.fill_(1.0)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        *_, ctx = job(solid, host_out=(Zh, Dh))
+        torch.cuda.synchronize()
+        e2e_s += time.perf_counter() - t0
+        ctx.close()
+    et = torch.tensor([e2e_s], dtype=torch.float64, device=dev)
+    if world > 1:
+        dist.all_reduce(et, op=dist.ReduceOp.MAX)
+    e2e_value = units_per_job * args.steps * world / float(et.item())
+
+    # roofline of the dominant kernel, from the live event timings above
+    peak, peak_kind = _peaks()
+    n_iface = int(info["n_interface"])
+    S = WORKLOAD["species"]
+    mp_bytes = n_fluid * (16 * S + 13) + n_iface * 16 * S         # per MP launch
+    lb_steps_mean = float(np.mean(lb_steps_all))
+    lb_bytes = n_fluid * 19 * 2 * 4                               # per LB launch
+    mp_launch_s = mp_ms / 1e3 / (args.steps * WORKLOAD["mp_steps"])
+    lb_launch_s = lb_ms / 1e3 / (args.steps * lb_steps_mean)
+    kern = {
+        "k_step<float>": {"share": mp_ms / total_ms, "avg_launch_us": mp_launch_s * 1e6,
+                          "algorithmic_bytes": mp_bytes, "gbs": mp_bytes / mp_launch_s / 1e9,
+                          "src": "mp.cu"},
+        "k_lb_step": {"share": lb_ms / total_ms, "avg_launch_us": lb_launch_s * 1e6,
+                      "algorithmic_bytes": lb_bytes, "gbs": lb_bytes / lb_launch_s / 1e9, "src": "lb.cu"},
+    }
+    dom = max(kern, key=lambda k: kern[k]["share"])
+    tr = TRAFFIC.get(dom)
+    traffic = tr["bytes_per_launch"] if tr and tr["src_sha"] == _src_sha(kern[dom]["src"]) else None
+    roofline = {"kernel": dom, "bound": "hbm", "achieved": kern[dom]["gbs"], "peak": peak, "unit": "GB/s",
+                "frac": kern[dom]["gbs"] / peak, "traffic": traffic,
+                "peak_source": f"{peak_kind} (MEASURED_PEAKS.json hbm_gbs)" if peak_kind == "measured"
+                else "fallback 6.8 TB/s"}
+
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": total_ms_max / args.steps, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "config": dict(WORKLOAD, n_fluid=n_fluid, n_interface=n_iface, spheres=nspheres,
+                       force_x=Fx, l2="256 MiB buffer written between timed jobs",
+                       parallelism="replicas" if world > 1 else "single GPU"),
+        "lb": {"steps_to_steady": lb_steps_all, "ms": lb_ms / args.steps,
+               "mlups": n_fluid * lb_steps_mean / (lb_ms / args.steps / 1e3) / 1e6},
+        "mp": {"ms": mp_ms / args.steps, "init_ms": init_ms / args.steps,
+               "kernel_rate": units_per_job / (mp_ms / args.steps / 1e3)},
+        "kernels": kern,
+        "roofline": roofline,
+        "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": 2 * int(solid.size),
+                "d2h_bytes_per_step": 2 * 8 * (WORKLOAD["mp_steps"] + 2)},
+        "gpu_launches": launches,
+        "clocks": clk,
+    }
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        line["cpu_baseline"] = oracle_sample(solid, int(round(lb_steps_mean)))
+        line["cpu_baseline"].pop("job_s_estimate", None)
+    if rank == 0:
+        print(json.dumps(line))
+    if world > 1:
+        dist.destroy_process_group()
+    return 0
+
+
+if __name__ == "__main__":
+    sys.exit(main())

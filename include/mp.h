@@ -1,0 +1,207 @@
+/*
+ * mp.h -- C ABI of libmp, the GB300 (sm_103a) library for the sorption-modified
+ * moment-propagation (MP) method of Levesque, Duvail, Pagonabarraga, Frenkel and
+ * Rotenberg, "Accounting for adsorption and desorption in Lattice Boltzmann simulations"
+ * (arXiv:1303.2470), and for the BGK lattice-Boltzmann solve that provides its flow.
+ *
+ * Conventions shared by every entry point
+ *  - Lattice units: dx = dt = 1. D3Q19 velocities (19 discrete velocities, Sec. "Algorithm").
+ *  - Lattice layout: node n = x + nx*(y + ny*z), x fastest; every axis is periodic.
+ *    Solid walls or grains are solid nodes of the mask.
+ *  - Velocity fields are FP32, structure of arrays: u[0..N) = u_x, u[N..2N) = u_y,
+ *    u[2N..3N) = u_z, zero on solid nodes.
+ *  - Pointers documented as "device" must be CUDA device (or managed) memory of the current
+ *    device; "host" pointers are ordinary host memory. Nothing is retained after a call
+ *    returns unless stated.
+ *  - Every function returns MP_OK (0) or a negative status, and never aborts the process.
+ *    The thread-local text of the last failure is returned by mp_last_error().
+ *  - Work is enqueued on the stream given in the options (NULL = the legacy default
+ *    stream). Calls that return results to host memory synchronise that stream.
+ */
+#ifndef MP_H
+#define MP_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* ---- status codes ------------------------------------------------------------------- */
+#define MP_OK 0
+#define MP_EINVAL (-1)        /* an argument is out of range or inconsistent             */
+#define MP_ENOMEM (-2)        /* a device or host allocation failed                       */
+#define MP_ECUDA (-3)         /* a CUDA runtime call or kernel launch failed              */
+#define MP_ENEGPROB (-4)      /* a link probability or a stay fraction is negative        */
+#define MP_ENOTCONVERGED (-5) /* lb_steady reached max_steps above its tolerance          */
+#define MP_ETIMEOUT (-6)      /* a bounded device-side wait gave up                       */
+
+/* ---- memory location of a caller pointer --------------------------------------------- */
+#define MP_HOST 0
+#define MP_DEVICE 1
+
+/* ---- storage / arithmetic precision of the propagated fields ------------------------- */
+#define MP_FP32 0 /* FP32 storage and arithmetic, FP64 reductions and D(t) (default)        */
+#define MP_FP64 1 /* FP64 storage, arithmetic and reductions                                */
+
+/* ---- initial density field ------------------------------------------------------------ */
+#define MP_INIT_EQUILIBRIUM 0 /* Boltzmann weights of Sec. "Algorithm" (free + adsorbed)    */
+#define MP_INIT_UNIFORM 1     /* 1/N_fluid on every free fluid node, nothing adsorbed       */
+
+#define MP_MAX_SPECIES 32 /* species (D_b, k_a, k_d sets) sharing one medium and flow      */
+
+/* A medium: the solid mask of an nx*ny*nz periodic lattice. */
+typedef struct {
+    int nx, ny, nz;       /* >= 3 each, nx*ny*nz < 2^31                                      */
+    const uint8_t* solid; /* nx*ny*nz bytes, nonzero = solid node                            */
+    int location;         /* MP_HOST or MP_DEVICE: where `solid` lives                       */
+} mp_geometry;
+
+/* Options of an MP context; mp_default_options() fills the defaults. */
+typedef struct {
+    int precision;      /* MP_FP32 (default) or MP_FP64                                      */
+    int directions;     /* velocity moments to propagate, bit mask 1 = x, 2 = y, 4 = z;
+                           0 means x only                                                   */
+    int init_density;   /* MP_INIT_EQUILIBRIUM (default) or MP_INIT_UNIFORM                 */
+    int allow_negative; /* 0: negative link probabilities fail mp_init with MP_ENEGPROB;
+                           1: they are only counted (see mp_info). A negative stay fraction
+                           always fails.                                                    */
+    int64_t capacity;   /* time points kept in the device Z(t)/D(t) series, >= 2;
+                           0 means 131072. mp_step fails once the series is full.           */
+    void* stream;       /* cudaStream_t of all work of the context; NULL = default stream   */
+} mp_options;
+
+void mp_default_options(mp_options* opt);
+
+typedef struct mp_ctx mp_ctx;
+
+/*
+ * mp_init -- set up the MP of one tracer species in a medium with a steady flow.
+ *
+ * Paper: Sec. "Algorithm": link probabilities p_i = f_i/rho - w_i + w_i lambda Q / 2 with
+ * Q = 1 and f_i/rho read as the D3Q19 equilibrium of the local velocity u; lambda = 12 D_b
+ * (D_b = lambda c_s^2 dt / 4); p_a = k_a dt/dx, p_d = k_d dt; Boltzmann weights (free
+ * 1/Z on the fluid, adsorbed K/Z on interfacial nodes, K = k_a/(k_d dx)); the velocity
+ * moment after the first step. Links into solid nodes carry no probability. Interfacial
+ * nodes are the fluid nodes with at least one solid D3Q19 neighbour.
+ *
+ *  out      receives the new context (host pointer to a handle); unchanged on failure.
+ *  g        the medium; g->solid is copied, so it may be freed after the call.
+ *  u        device, FP32, 3*N, SoA; NULL = fluid at rest. Copied at the call.
+ *  D_b      bulk diffusion coefficient, 0 < D_b <= 1/8.
+ *  k_a,k_d  adsorption (length/time) and desorption (1/time) rates, in [0, 1]; the
+ *           equilibrium start needs k_d > 0 whenever k_a > 0.
+ *  opt      options, NULL = defaults.
+ * After the call the density and velocity-moment fields are at t = 1 and the series hold
+ * Z(0), Z(1), D(0) = Z(0)/2, D(1) = D(0) + Z(1). Allocates all device memory of the context.
+ * Errors: MP_EINVAL, MP_ENOMEM, MP_ECUDA, MP_ENEGPROB.
+ */
+int mp_init(mp_ctx** out, const mp_geometry* g, const float* u, double D_b, double k_a,
+            double k_d, const mp_options* opt);
+
+/*
+ * mp_init_batch -- as mp_init for n_species species (1..MP_MAX_SPECIES) that share the
+ * medium and the flow; D_b, k_a, k_d are host arrays of n_species values. All species
+ * advance together in every mp_step.
+ */
+int mp_init_batch(mp_ctx** out, const mp_geometry* g, const float* u, int n_species,
+                  const double* D_b, const double* k_a, const double* k_d,
+                  const mp_options* opt);
+
+/*
+ * mp_step -- advance every species and field n >= 0 steps t -> t+1.
+ *
+ * Paper: Sec. "Algorithm", Eq. (propagated_quantity) for P*, Eq. (Pads) and Eq. (newP) for
+ * the exchange with the adsorbed population on interfacial nodes, with the adsorbed share
+ * removed from the stay fraction (1 - sum_i p_i - p_a) so that total mass is conserved;
+ * then Z_g(t+1) = sum_r P_g(r,t+1) sum_i p_i(r) c_ig (last equation of that section) and
+ * D(t+1) = D(t) + Z(t+1) (Eq. D_t_from_vacf as a sum over steps), both in FP64.
+ * Asynchronous on the context's stream. Errors: MP_EINVAL (n < 0, or the series would
+ * exceed its capacity), MP_ECUDA.
+ */
+int mp_step(mp_ctx* c, int64_t n);
+
+/*
+ * mp_vacf -- copy the series Z_g(t) and D_g(t), t = 0..T, of one species and direction to
+ * host memory (synchronises the stream).
+ *  species    0..n_species-1;  direction 0 = x, 1 = y, 2 = z (must be propagated).
+ *  Z, D       host arrays of cap doubles each (either may be NULL).
+ *  n_out      receives T+1, the number of time points available (may exceed cap; then
+ *             only the first cap are written).
+ * Errors: MP_EINVAL, MP_ECUDA.
+ */
+int mp_vacf(mp_ctx* c, int species, int direction, double* Z, double* D, int64_t cap,
+            int64_t* n_out);
+
+/*
+ * mp_mass -- FP64 sums of the density field of one species (synchronises the stream):
+ *  out[0] = sum over fluid nodes of P, out[1] = sum over interfacial nodes of Gamma
+ *  (P_ads), out[2] = sum over interfacial nodes of P. Total mass out[0] + out[1] is
+ *  conserved by the step; out[1]/out[2] tends to K = k_a/k_d at equilibrium.
+ */
+int mp_mass(mp_ctx* c, int species, double out[3]);
+
+typedef struct {
+    int64_t n_nodes;          /* N = nx*ny*nz                                           */
+    int64_t n_fluid;          /* fluid nodes                                            */
+    int64_t n_interface;      /* interfacial fluid nodes                                */
+    int64_t n_negative_links; /* open links with p_i < 0, summed over species           */
+    int64_t t;                /* current time of the fields (1 after mp_init)           */
+    int n_species;
+    int n_fields;             /* 1 + number of velocity moments                         */
+    int precision;
+} mp_info_t;
+
+int mp_info(mp_ctx* c, mp_info_t* info);
+
+/*
+ * mp_get_field / mp_set_field -- copy one propagated field of one species between the
+ * device and dense host arrays (for checks and checkpoints; synchronises the stream).
+ *  field 0 = density P; field k >= 1 = k-th propagated velocity moment (x, y, z order).
+ *  free_dense  host, N doubles: the free field (zero on solid nodes).
+ *  ads_dense   host, N doubles or NULL: the adsorbed partner, zero off the interface.
+ * mp_set_field ignores solid nodes and non-interfacial entries of ads_dense.
+ */
+int mp_get_field(mp_ctx* c, int species, int field, double* free_dense, double* ads_dense);
+int mp_set_field(mp_ctx* c, int species, int field, const double* free_dense,
+                 const double* ads_dense);
+
+/* mp_free -- release a context and all its device memory (NULL is accepted). */
+void mp_free(mp_ctx* c);
+
+/* Text of the calling thread's last failure ("" if none); valid until its next call. */
+const char* mp_last_error(void);
+
+/*
+ * lb_steady -- steady BGK lattice-Boltzmann flow through a medium.
+ *
+ * Paper: Eq. (lb_evolution), f_i(r + c_i dt, t + dt) = f_i(r,t) + Delta_i(r,t), with a BGK
+ * collision Delta_i = -(f_i - f_i^eq)/tau, the Guo body-force term for a uniform force F on
+ * fluid nodes, u = (sum_i f_i c_i + F/2)/rho, and halfway bounce-back on links into solid
+ * nodes. Populations are stored in FP32 as deviations f_i - w_i; the residual is FP64.
+ *
+ *  g             the medium (host or device mask; copied for the call).
+ *  force         host, 3 doubles: body force per node.
+ *  tau           relaxation time, > 1/2.
+ *  tol           stop at the first checked step t with max |u(t) - u(t-1)| < tol, taken
+ *                over fluid nodes and components.
+ *  max_steps     step budget (>= 1); check_every: residual period (>= 1); the residual is
+ *                also taken at t = max_steps.
+ *  u_init        device, FP32 3*N, or NULL: start from f^eq(rho = 1, u_init) (cold start
+ *                from rest when NULL).
+ *  u_out         device, FP32 3*N: u at the final step, zero on solid nodes.
+ *  steps_out, residual_out   host (either may be NULL): steps taken, last residual.
+ *  stream        cudaStream_t or NULL. Allocates its working populations stream-ordered
+ *                and frees them before returning; synchronises the stream.
+ * Returns MP_OK when converged, MP_ENOTCONVERGED when max_steps ran out (u_out, steps_out
+ * and residual_out are still written), MP_EINVAL, MP_ENOMEM or MP_ECUDA.
+ */
+int lb_steady(const mp_geometry* g, const double force[3], double tau, double tol,
+              int64_t max_steps, int64_t check_every, const float* u_init, float* u_out,
+              int64_t* steps_out, double* residual_out, void* stream);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* MP_H */

@@ -1,0 +1,224 @@
+// lb.cu -- steady BGK lattice-Boltzmann flow (paper Eq. lb_evolution) for the velocity
+// field that biases the moment propagation. One fused pull step per launch:
+//   stream   f_i(r) <- f_i^post(r - c_i), or f_ibar^post(r) when r - c_i is solid
+//            (halfway bounce-back, ibar the opposite link);
+//   moments  rho = sum f_i, u = (sum f_i c_i + F/2) / rho;
+//   collide  f_i^post = f_i - (f_i - f_i^eq(rho,u))/tau
+//                       + (1 - 1/(2 tau)) w_i [3 (c_i - u) + 9 (c_i.u) c_i].F   (Guo force).
+// Populations are FP32 deviations g_i = f_i - w_i, structure of arrays g[i*N + n], which
+// keeps ~9 significant digits of the O(u) part that sets the velocity. Only fluid nodes
+// are read or written. The steady criterion max|u(t) - u(t-1)| is evaluated in FP64.
+#include <cmath>
+#include <cstring>
+#include <string>
+
+#include "internal.cuh"
+
+using namespace mp;
+
+namespace {
+
+constexpr int kLbThreads = 256;
+
+struct LbArgs {
+    int nx, ny, nz, N;
+    const uint32_t* fluid;
+    float Fx, Fy, Fz;
+    float inv_tau;
+    float guo;  // 1 - 1/(2 tau)
+};
+
+__device__ __forceinline__ bool lb_bit(const uint32_t* __restrict__ w, int n)
+{
+    return (__ldg(w + (n >> 5)) >> (n & 31)) & 1u;
+}
+__device__ __forceinline__ int lb_wrap(int v, int n) { return v < 0 ? v + n : (v >= n ? v - n : v); }
+
+// mode 0: plain step; 1: also store u into u_prev; 2: store u into u_out, fold
+// max|u - u_prev| (FP64) into *res_bits (non-negative doubles order like their bits), then
+// store u into u_prev.
+__global__ void __launch_bounds__(kLbThreads)
+    k_lb_step(const LbArgs a, const float* __restrict__ g, float* __restrict__ gn, int mode,
+              float* __restrict__ u_prev, float* __restrict__ u_out, unsigned long long* __restrict__ res_bits)
+{
+    const int n = blockIdx.x * kLbThreads + threadIdx.x;
+    double res = 0.0;
+    if (n < a.N) {
+        if (!lb_bit(a.fluid, n)) {
+            if (mode == 2) u_out[n] = u_out[a.N + n] = u_out[2 * a.N + n] = 0.0f;
+        } else {
+            const int x = n % a.nx, y = (n / a.nx) % a.ny, z = n / (a.nx * a.ny);
+            float f[kQ];
+#pragma unroll
+            for (int i = 0; i < kQ; ++i) {
+                if (i == 0) {
+                    f[0] = g[n];
+                } else {
+                    const int s = lb_wrap(x - cx(i), a.nx) +
+                                  a.nx * (lb_wrap(y - cy(i), a.ny) + a.ny * lb_wrap(z - cz(i), a.nz));
+                    f[i] = lb_bit(a.fluid, s) ? g[(size_t)i * a.N + s] : g[(size_t)opposite(i) * a.N + n];
+                }
+            }
+            float drho = 0.f, mx = 0.f, my = 0.f, mz = 0.f;
+#pragma unroll
+            for (int i = 0; i < kQ; ++i) {
+                drho += f[i];
+                mx += float(cx(i)) * f[i];
+                my += float(cy(i)) * f[i];
+                mz += float(cz(i)) * f[i];
+            }
+            const float rho = 1.0f + drho;
+            const float inv_rho = 1.0f / rho;
+            const float ux = (mx + 0.5f * a.Fx) * inv_rho;
+            const float uy = (my + 0.5f * a.Fy) * inv_rho;
+            const float uz = (mz + 0.5f * a.Fz) * inv_rho;
+            const float uu = ux * ux + uy * uy + uz * uz;
+            const float uF = ux * a.Fx + uy * a.Fy + uz * a.Fz;
+#pragma unroll
+            for (int i = 0; i < kQ; ++i) {
+                const float w = weight<float>(i);
+                const float cu = float(cx(i)) * ux + float(cy(i)) * uy + float(cz(i)) * uz;
+                const float cF = float(cx(i)) * a.Fx + float(cy(i)) * a.Fy + float(cz(i)) * a.Fz;
+                // f^eq - w = w [(rho - 1) + rho (3 cu + 4.5 cu^2 - 1.5 uu)]
+                const float geq = w * (drho + rho * (3.0f * cu + 4.5f * cu * cu - 1.5f * uu));
+                const float src = a.guo * w * (3.0f * (cF - uF) + 9.0f * cu * cF);
+                gn[(size_t)i * a.N + n] = f[i] - a.inv_tau * (f[i] - geq) + src;
+            }
+            if (mode == 1) {
+                u_prev[n] = ux;
+                u_prev[a.N + n] = uy;
+                u_prev[2 * a.N + n] = uz;
+            } else if (mode == 2) {
+                u_out[n] = ux;
+                u_out[a.N + n] = uy;
+                u_out[2 * a.N + n] = uz;
+                res = fmax(fabs((double)ux - (double)u_prev[n]),
+                           fmax(fabs((double)uy - (double)u_prev[a.N + n]), fabs((double)uz - (double)u_prev[2 * a.N + n])));
+                // this node's u(t) is the reference of the next check when it is due next step
+                u_prev[n] = ux;
+                u_prev[a.N + n] = uy;
+                u_prev[2 * a.N + n] = uz;
+            }
+        }
+    }
+    if (mode == 2) {
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) res = fmax(res, __shfl_xor_sync(0xffffffffu, res, o));
+        if ((threadIdx.x & 31) == 0 && res > 0.0) atomicMax(res_bits, (unsigned long long)__double_as_longlong(res));
+    }
+}
+
+// f = f^eq(rho = 1, u0) (u0 = 0 when NULL) as deviations; u_prev = u0
+__global__ void k_lb_init(const LbArgs a, const float* __restrict__ u0, float* __restrict__ g, float* __restrict__ u_prev)
+{
+    const int n = blockIdx.x * blockDim.x + threadIdx.x;
+    if (n >= a.N) return;
+    const bool fl = lb_bit(a.fluid, n);
+    float ux = 0.f, uy = 0.f, uz = 0.f;
+    if (u0 && fl) {
+        ux = u0[n];
+        uy = u0[a.N + n];
+        uz = u0[2 * a.N + n];
+    }
+    const float uu = ux * ux + uy * uy + uz * uz;
+#pragma unroll
+    for (int i = 0; i < kQ; ++i) {
+        const float cu = float(cx(i)) * ux + float(cy(i)) * uy + float(cz(i)) * uz;
+        g[(size_t)i * a.N + n] = fl ? weight<float>(i) * (3.0f * cu + 4.5f * cu * cu - 1.5f * uu) : 0.0f;
+    }
+    u_prev[n] = ux;
+    u_prev[a.N + n] = uy;
+    u_prev[2 * a.N + n] = uz;
+}
+
+}  // namespace
+
+extern "C" int lb_steady(const mp_geometry* geom, const double force[3], double tau, double tol, int64_t max_steps,
+                         int64_t check_every, const float* u_init, float* u_out, int64_t* steps_out,
+                         double* residual_out, void* stream_ptr)
+{
+    clear_error();
+    if (!force || !u_out || !(tau > 0.5) || max_steps < 1 || check_every < 1 || !(tol >= 0.0)) {
+        set_error("lb_steady: need force, u_out, tau > 1/2, tol >= 0, max_steps >= 1, check_every >= 1");
+        return MP_EINVAL;
+    }
+    cudaStream_t s = (cudaStream_t)stream_ptr;
+    Geometry G;
+    int rc = build_geometry(geom, s, true, false, &G);
+    if (rc != MP_OK) return rc;
+    const size_t N = (size_t)G.N;
+    float *g0 = nullptr, *g1 = nullptr, *uprev = nullptr;
+    unsigned long long* res_d = nullptr;
+    cudaError_t e = cudaMallocAsync((void**)&g0, sizeof(float) * kQ * N, s);
+    if (e == cudaSuccess) e = cudaMallocAsync((void**)&g1, sizeof(float) * kQ * N, s);
+    if (e == cudaSuccess) e = cudaMallocAsync((void**)&uprev, sizeof(float) * 3 * N, s);
+    if (e == cudaSuccess) e = cudaMallocAsync((void**)&res_d, sizeof(unsigned long long), s);
+    auto cleanup = [&]() {
+        if (g0) cudaFreeAsync(g0, s);
+        if (g1) cudaFreeAsync(g1, s);
+        if (uprev) cudaFreeAsync(uprev, s);
+        if (res_d) cudaFreeAsync(res_d, s);
+        free_geometry(&G, s, true);
+        cudaStreamSynchronize(s);
+    };
+    if (e != cudaSuccess) {
+        rc = cuda_fail(e, "lb_steady allocation");
+        cleanup();
+        return rc;
+    }
+    LbArgs a;
+    a.nx = G.nx;
+    a.ny = G.ny;
+    a.nz = G.nz;
+    a.N = G.N;
+    a.fluid = G.fluid;
+    a.Fx = (float)force[0];
+    a.Fy = (float)force[1];
+    a.Fz = (float)force[2];
+    a.inv_tau = (float)(1.0 / tau);
+    a.guo = (float)(1.0 - 0.5 / tau);
+    const int blocks = (G.N + kLbThreads - 1) / kLbThreads;
+    k_lb_init<<<blocks, kLbThreads, 0, s>>>(a, u_init, g0, uprev);
+    e = cudaGetLastError();
+    int64_t t = 0;
+    double res = INFINITY;
+    bool converged = false;
+    while (e == cudaSuccess && t < max_steps) {
+        const int64_t t1 = t + 1;
+        int mode = 0;
+        if (t1 % check_every == 0 || t1 == max_steps)
+            mode = 2;
+        else if ((t1 + 1) % check_every == 0 || t1 + 1 == max_steps)
+            mode = 1;
+        if (mode == 2) e = cudaMemsetAsync(res_d, 0, sizeof(unsigned long long), s);
+        k_lb_step<<<blocks, kLbThreads, 0, s>>>(a, g0, g1, mode, uprev, u_out, res_d);
+        if (e == cudaSuccess) e = cudaGetLastError();
+        float* tmp = g0;
+        g0 = g1;
+        g1 = tmp;
+        t = t1;
+        if (mode == 2 && e == cudaSuccess) {
+            unsigned long long bits = 0;
+            e = cudaMemcpyAsync(&bits, res_d, sizeof(bits), cudaMemcpyDeviceToHost, s);
+            if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+            memcpy(&res, &bits, sizeof(res));
+            if (res < tol) {
+                converged = true;
+                break;
+            }
+        }
+    }
+    if (e != cudaSuccess) {
+        rc = cuda_fail(e, "lb_steady step");
+        cleanup();
+        return rc;
+    }
+    cleanup();
+    if (steps_out) *steps_out = t;
+    if (residual_out) *residual_out = res;
+    if (!converged) {
+        set_error("lb_steady: residual " + std::to_string(res) + " above tol after " + std::to_string(t) + " steps");
+        return MP_ENOTCONVERGED;
+    }
+    return MP_OK;
+}

@@ -1,0 +1,858 @@
+// mp.cu -- sorption-modified moment propagation on the GPU (paper Sec. "Algorithm"):
+// the initialisation of the density and velocity-moment fields, the fused propagation +
+// sorption step with its FP64 VACF / D(t) reduction, and the C-ABI context functions.
+//
+// Per fluid node r and step (Eq. propagated_quantity, Eqs. Pads and newP):
+//   P*(r)      = sum_i X(r - c_i) p_i(r - c_i) + X(r) (1 - sum_i p_i(r) - p_a 1_I(r))
+//   Xa(r,t+1)  = p_a X(r) + (1 - p_d) Xa(r)            on interfacial nodes
+//   X(r,t+1)   = P*(r) + p_d Xa(r)                      on interfacial nodes
+// with p_i(s) = w_i [lambda/2 + 3 c_i.u(s) + 9/2 (c_i.u(s))^2 - 3/2 u(s).u(s)] on links
+// whose far end is fluid, zero otherwise; lambda = 12 D_b; p_a = k_a, p_d = k_d. Every
+// species sharing the medium uses the same advective part of p_i, which is computed once
+// per link and node; only lambda/2, p_a and p_d differ per species.
+// The VACF of direction g is Z_g(t) = sum_r P_g(r,t) u*_g(r), u*_g(r) = sum_i p_i(r) c_ig.
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "internal.cuh"
+
+namespace mp {
+const char* last_error_text();
+}
+
+using namespace mp;
+
+namespace {
+
+constexpr int kThreads = 256;
+constexpr int kWarps = kThreads / 32;
+constexpr int kMaxF = 4;  // density + up to three velocity moments
+
+template <typename T>
+struct Args {
+    int nx, ny, nz, N, NI;
+    const uint32_t* fluid;
+    const uint32_t* iface;
+    const int32_t* ibase;
+    const T* u;  // 3*N SoA
+    int S, F, M;
+    int dir[3];  // direction of velocity moment m (field m+1)
+    T hl[MP_MAX_SPECIES];  // lambda/2
+    T pa[MP_MAX_SPECIES];
+    T pd[MP_MAX_SPECIES];
+    double* partials;      // [gridDim.x][K]
+    unsigned int* ticket;  // blocks done in the current launch
+    double* Z;             // [K_series][cap]
+    double* D;
+    long long* tdev;  // time index of the last written series entry
+    long long cap;
+};
+
+struct InitExtra {
+    double invZ[MP_MAX_SPECIES];  // 1 / partition function (free weight per fluid node)
+    double K[MP_MAX_SPECIES];     // k_a / k_d (0 without sorption)
+    double inv_nf;                // 1 / N_fluid
+    int uniform;                  // density starts uniform-free
+};
+
+__device__ __forceinline__ bool bit_of(const uint32_t* __restrict__ w, int n)
+{
+    return (__ldg(w + (n >> 5)) >> (n & 31)) & 1u;
+}
+__device__ __forceinline__ int wrap(int v, int n) { return v < 0 ? v + n : (v >= n ? v - n : v); }
+
+// What a fluid node needs from its own links and its 18 upstream neighbours.
+template <typename T>
+struct Node {
+    T coef[kQ];   // advective part of p_i at the source r - c_i (i >= 1)
+    int src[kQ];  // source node r - c_i, -1 when it is solid (no inflow on that link)
+    T SA, SW;     // sum over open links of w_i adv_i(r), of w_i
+    T UA[3], UW[3];  // sum over open links of w_i adv_i(r) c_ig, of w_i c_ig
+    T QA[3], QW[3];  // same with c_ig^2 (Z(0) only)
+    bool itf;
+    int aidx;  // compact index among interfacial nodes
+};
+
+template <typename T>
+__device__ __forceinline__ T advective(int i, T ux, T uy, T uz, T uu)
+{
+    T e = T(cx(i)) * ux + T(cy(i)) * uy + T(cz(i)) * uz;
+    return weight<T>(i) * (T(3) * e + T(4.5) * e * e - T(1.5) * uu);
+}
+
+template <typename T, bool kWithQ>
+__device__ __forceinline__ void load_node(const Args<T>& a, int n, Node<T>& d)
+{
+    const int x = n % a.nx, y = (n / a.nx) % a.ny, z = n / (a.nx * a.ny);
+    const T ux = a.u[n], uy = a.u[a.N + n], uz = a.u[2 * a.N + n];
+    const T uu = ux * ux + uy * uy + uz * uz;
+    d.SA = d.SW = T(0);
+#pragma unroll
+    for (int g = 0; g < 3; ++g) d.UA[g] = d.UW[g] = d.QA[g] = d.QW[g] = T(0);
+    d.itf = false;
+#pragma unroll
+    for (int i = 1; i < kQ; ++i) {
+        // outgoing link: open iff r + c_i is fluid
+        const int t = wrap(x + cx(i), a.nx) + a.nx * (wrap(y + cy(i), a.ny) + a.ny * wrap(z + cz(i), a.nz));
+        if (bit_of(a.fluid, t)) {
+            const T ad = advective<T>(i, ux, uy, uz, uu);
+            d.SA += ad;
+            d.SW += weight<T>(i);
+#pragma unroll
+            for (int g = 0; g < 3; ++g) {
+                if (ci(i, g) != 0) {
+                    d.UA[g] += ad * T(ci(i, g));
+                    d.UW[g] += weight<T>(i) * T(ci(i, g));
+                    if (kWithQ) {
+                        d.QA[g] += ad;
+                        d.QW[g] += weight<T>(i);
+                    }
+                }
+            }
+        } else {
+            d.itf = true;
+        }
+        // incoming link: from s = r - c_i
+        const int s = wrap(x - cx(i), a.nx) + a.nx * (wrap(y - cy(i), a.ny) + a.ny * wrap(z - cz(i), a.nz));
+        if (bit_of(a.fluid, s)) {
+            const T sx = a.u[s], sy = a.u[a.N + s], sz = a.u[2 * a.N + s];
+            d.coef[i] = advective<T>(i, sx, sy, sz, sx * sx + sy * sy + sz * sz);
+            d.src[i] = s;
+        } else {
+            d.coef[i] = T(0);
+            d.src[i] = -1;
+        }
+    }
+    d.aidx = 0;
+    if (d.itf) {
+        const uint32_t bits = __ldg(a.iface + (n >> 5));
+        d.aidx = __ldg(a.ibase + (n >> 5)) + __popc(bits & ((1u << (n & 31)) - 1u));
+    }
+}
+
+template <typename T>
+__device__ __forceinline__ T pick(const T v[3], int g)
+{
+    return g == 0 ? v[0] : (g == 1 ? v[1] : v[2]);
+}
+
+template <typename T>
+__device__ __forceinline__ T warp_sum(T v)
+{
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    return v;
+}
+
+// Sum `cnt` per-thread values over the block: warp sums in T (FP32 or FP64), then FP64
+// across warps in fixed order; thread j < cnt writes the total of value j to out[j].
+template <typename T, int kMax>
+__device__ __forceinline__ void block_sum_store(const T (&v)[kMax], int cnt, double* out)
+{
+    __shared__ double s_red[kWarps][2 * kMaxF];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+#pragma unroll
+    for (int j = 0; j < kMax; ++j) {
+        if (j < cnt) {
+            T w = warp_sum(v[j]);
+            if (lane == 0) s_red[warp][j] = (double)w;
+        }
+    }
+    __syncthreads();
+    if (threadIdx.x < cnt) {
+        double tot = 0.0;
+        for (int k = 0; k < kWarps; ++k) tot += s_red[k][threadIdx.x];
+        out[threadIdx.x] = tot;
+    }
+    __syncthreads();
+}
+
+// Last block of the grid: FP64 sum of the per-block partials of each of the K series
+// values, in a fixed order; `emit(k, total)` is called by thread 0.
+template <typename Emit>
+__device__ __forceinline__ bool grid_total(double* partials, int K, unsigned int* ticket, Emit emit)
+{
+    __shared__ unsigned int s_last;
+    __shared__ double s_red[kWarps];
+    __threadfence();
+    __syncthreads();
+    if (threadIdx.x == 0) s_last = (atomicAdd(ticket, 1u) == gridDim.x - 1) ? 1u : 0u;
+    __syncthreads();
+    if (!s_last) return false;
+    __threadfence();
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    for (int k = 0; k < K; ++k) {
+        double v = 0.0;
+        for (int b = threadIdx.x; b < (int)gridDim.x; b += kThreads) v += __ldcg(partials + (size_t)b * K + k);
+        v = warp_sum(v);
+        if (lane == 0) s_red[warp] = v;
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            double tot = 0.0;
+            for (int w = 0; w < kWarps; ++w) tot += s_red[w];
+            emit(k, tot);
+        }
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) *ticket = 0u;
+    return true;
+}
+
+// ---------------------------------------------------------------------------------------
+// Step t -> t+1 of every species and field, fused with Z_g(t+1) and D_g(t+1).
+// ---------------------------------------------------------------------------------------
+template <typename T>
+__global__ void __launch_bounds__(kThreads)
+    k_step(const Args<T> a, const T* __restrict__ P, T* __restrict__ Pn, const T* __restrict__ A,
+           T* __restrict__ An)
+{
+    const int n = blockIdx.x * kThreads + threadIdx.x;
+    const bool active = n < a.N && bit_of(a.fluid, n);
+    Node<T> d;
+    if (active) load_node<T, false>(a, n, d);
+    const int K = a.S * a.M;
+    for (int sp = 0; sp < a.S; ++sp) {
+        const T hl = a.hl[sp], pa = a.pa[sp], pd = a.pd[sp];
+        T zp[kMaxF] = {T(0), T(0), T(0), T(0)};
+        if (active) {
+            const T stay = T(1) - d.SA - hl * d.SW - (d.itf ? pa : T(0));
+#pragma unroll
+            for (int f = 0; f < kMaxF; ++f) {
+                if (f < a.F) {
+                    const size_t base = (size_t)(sp * a.F + f) * a.N;
+                    const T* X = P + base;
+                    T acc = T(0);
+#pragma unroll
+                    for (int i = 1; i < kQ; ++i)
+                        if (d.src[i] >= 0) acc += (d.coef[i] + weight<T>(i) * hl) * __ldg(X + d.src[i]);
+                    const T xr = __ldg(X + n);
+                    T xn = acc + stay * xr;
+                    if (d.itf) {
+                        const size_t ai = (size_t)(sp * a.F + f) * a.NI + d.aidx;
+                        const T xa = A[ai];
+                        xn += pd * xa;
+                        An[ai] = pa * xr + (T(1) - pd) * xa;
+                    }
+                    Pn[base + n] = xn;
+                    if (f >= 1) {
+                        const int g = a.dir[f - 1];
+                        zp[f - 1] = xn * (pick(d.UA, g) + hl * pick(d.UW, g));
+                    }
+                }
+            }
+        }
+        block_sum_store<T, kMaxF>(zp, a.M, a.partials + (size_t)blockIdx.x * K + sp * a.M);
+    }
+    const long long cap = a.cap;
+    double* Z = a.Z;
+    double* D = a.D;
+    long long* tdev = a.tdev;
+    __shared__ long long s_t1;
+    if (threadIdx.x == 0) s_t1 = *((volatile long long*)tdev) + 1;
+    // s_t1 is only read by thread 0 of the last block, after the barriers in grid_total
+    bool last = grid_total(a.partials, K, a.ticket, [&](int k, double tot) {
+        const long long t1 = s_t1;
+        Z[(size_t)k * cap + t1] = tot;
+        D[(size_t)k * cap + t1] = D[(size_t)k * cap + t1 - 1] + tot;
+    });
+    if (last && threadIdx.x == 0) *tdev = s_t1;
+}
+
+// ---------------------------------------------------------------------------------------
+// Initialisation: density at t = 1 (one step from its t = 0 state), velocity moments at
+// t = 1 (P_g(r,1) = sum_i pi(r - c_i) p_i(r - c_i) c_ig, no adsorbed share), Z_g(0), Z_g(1).
+// The free Boltzmann weight pi = 1/Z is the same on every fluid node (neutral tracer).
+// ---------------------------------------------------------------------------------------
+template <typename T>
+__global__ void __launch_bounds__(kThreads)
+    k_init(const Args<T> a, const InitExtra b, T* __restrict__ P1, T* __restrict__ A1)
+{
+    const int n = blockIdx.x * kThreads + threadIdx.x;
+    const bool active = n < a.N && bit_of(a.fluid, n);
+    Node<T> d;
+    if (active) load_node<T, true>(a, n, d);
+    const int K2 = 2 * a.S * a.M;
+    for (int sp = 0; sp < a.S; ++sp) {
+        const T hl = a.hl[sp], pa = a.pa[sp], pd = a.pd[sp];
+        const T invZ = (T)b.invZ[sp];
+        T zp[2 * kMaxF] = {T(0), T(0), T(0), T(0), T(0), T(0), T(0), T(0)};
+        if (active) {
+            const T stay = T(1) - d.SA - hl * d.SW - (d.itf ? pa : T(0));
+            // density field: X0 uniform over the free fluid (1/N_f or the free weight 1/Z),
+            // adsorbed K/Z on the interface for the equilibrium start
+            const T x0 = b.uniform ? (T)b.inv_nf : invZ;
+            const T xa0 = (b.uniform || !d.itf) ? T(0) : (T)b.K[sp] * invZ;
+            T inflow = T(0);
+#pragma unroll
+            for (int i = 1; i < kQ; ++i)
+                if (d.src[i] >= 0) inflow += (d.coef[i] + weight<T>(i) * hl) * x0;
+            T xn = inflow + stay * x0;
+            if (d.itf) {
+                const size_t ai = (size_t)(sp * a.F) * a.NI + d.aidx;
+                xn += pd * xa0;
+                A1[ai] = pa * x0 + (T(1) - pd) * xa0;
+            }
+            P1[(size_t)(sp * a.F) * a.N + n] = xn;
+#pragma unroll
+            for (int m = 0; m < kMaxF - 1; ++m) {
+                if (m < a.M) {
+                    const int g = a.dir[m];
+                    T pg = T(0);
+#pragma unroll
+                    for (int i = 1; i < kQ; ++i)
+                        if (d.src[i] >= 0 && ci(i, g) != 0)
+                            pg += (d.coef[i] + weight<T>(i) * hl) * T(ci(i, g)) * invZ;
+                    P1[(size_t)(sp * a.F + 1 + m) * a.N + n] = pg;
+                    if (d.itf) A1[(size_t)(sp * a.F + 1 + m) * a.NI + d.aidx] = T(0);
+                    zp[2 * m] = invZ * (pick(d.QA, g) + hl * pick(d.QW, g));
+                    zp[2 * m + 1] = pg * (pick(d.UA, g) + hl * pick(d.UW, g));
+                }
+            }
+        }
+        block_sum_store<T, 2 * kMaxF>(zp, 2 * a.M, a.partials + (size_t)blockIdx.x * K2 + sp * 2 * a.M);
+    }
+    const long long cap = a.cap;
+    double* Z = a.Z;
+    double* D = a.D;
+    bool last = grid_total(a.partials, K2, a.ticket, [&](int k, double tot) {
+        const int series = k / 2;
+        if ((k & 1) == 0) {
+            Z[(size_t)series * cap + 0] = tot;
+            D[(size_t)series * cap + 0] = tot / 2.0;
+        } else {
+            Z[(size_t)series * cap + 1] = tot;
+            D[(size_t)series * cap + 1] = D[(size_t)series * cap + 0] + tot;
+        }
+    });
+    if (last && threadIdx.x == 0) *a.tdev = 1;
+}
+
+// Count open links with p_i < 0 and nodes with a negative stay fraction, per species.
+template <typename T>
+__global__ void __launch_bounds__(kThreads)
+    k_negative(const Args<T> a, unsigned long long* __restrict__ counts)
+{
+    const int n = blockIdx.x * kThreads + threadIdx.x;
+    if (n >= a.N || !bit_of(a.fluid, n)) return;
+    const int x = n % a.nx, y = (n / a.nx) % a.ny, z = n / (a.nx * a.ny);
+    const T ux = a.u[n], uy = a.u[a.N + n], uz = a.u[2 * a.N + n];
+    const T uu = ux * ux + uy * uy + uz * uz;
+    for (int sp = 0; sp < a.S; ++sp) {
+        unsigned neg = 0;
+        T out = T(0);
+        bool itf = false;
+#pragma unroll
+        for (int i = 1; i < kQ; ++i) {
+            const int t = wrap(x + cx(i), a.nx) + a.nx * (wrap(y + cy(i), a.ny) + a.ny * wrap(z + cz(i), a.nz));
+            if (bit_of(a.fluid, t)) {
+                const T p = advective<T>(i, ux, uy, uz, uu) + weight<T>(i) * a.hl[sp];
+                neg += p < T(0);
+                out += p;
+            } else {
+                itf = true;
+            }
+        }
+        const T stay = T(1) - out - (itf ? a.pa[sp] : T(0));
+        if (neg) atomicAdd(&counts[0], (unsigned long long)neg);
+        if (stay < T(0)) atomicAdd(&counts[1], 1ull);
+    }
+}
+
+// FP64 per-block partial sums of the density field of one species: sum_F P, sum_I Gamma,
+// sum_I P.
+template <typename T>
+__global__ void __launch_bounds__(kThreads)
+    k_mass(const Args<T> a, const T* __restrict__ P, const T* __restrict__ A, double* __restrict__ out)
+{
+    const int n = blockIdx.x * kThreads + threadIdx.x;
+    double v[3] = {0.0, 0.0, 0.0};
+    if (n < a.N && bit_of(a.fluid, n)) {
+        v[0] = (double)P[n];
+        const uint32_t bits = __ldg(a.iface + (n >> 5));
+        if ((bits >> (n & 31)) & 1u) {
+            const int k = __ldg(a.ibase + (n >> 5)) + __popc(bits & ((1u << (n & 31)) - 1u));
+            v[1] = (double)A[k];
+            v[2] = v[0];
+        }
+    }
+    __shared__ double s[3][kWarps];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+#pragma unroll
+    for (int j = 0; j < 3; ++j) {
+        double w = warp_sum(v[j]);
+        if (lane == 0) s[j][warp] = w;
+    }
+    __syncthreads();
+    if (threadIdx.x < 3) {
+        double t = 0.0;
+        for (int k = 0; k < kWarps; ++k) t += s[threadIdx.x][k];
+        out[(size_t)blockIdx.x * 3 + threadIdx.x] = t;
+    }
+}
+
+template <typename T>
+__global__ void k_convert_u(const float* __restrict__ in, T* __restrict__ out, const uint32_t* __restrict__ fluid,
+                            int N)
+{
+    int k = blockIdx.x * blockDim.x + threadIdx.x;
+    if (k >= 3 * N) return;
+    int n = k % N;
+    out[k] = (in && bit_of(fluid, n)) ? (T)in[k] : T(0);
+}
+
+}  // namespace
+
+// ---------------------------------------------------------------------------------------
+// Context and C ABI
+// ---------------------------------------------------------------------------------------
+struct mp_ctx {
+    Geometry geo;
+    int precision = MP_FP32;
+    int S = 0, F = 0, M = 0;
+    int dir[3] = {0, 0, 0};
+    cudaStream_t stream = nullptr;
+    long long cap = 0;
+    long long t = 0;
+    double Db[MP_MAX_SPECIES], ka[MP_MAX_SPECIES], kd[MP_MAX_SPECIES];
+    void* u = nullptr;
+    void* P[2] = {nullptr, nullptr};
+    void* A[2] = {nullptr, nullptr};
+    int cur = 0;
+    double* Z = nullptr;
+    double* D = nullptr;
+    long long* tdev = nullptr;
+    double* partials = nullptr;
+    unsigned int* ticket = nullptr;
+    int blocks = 0;
+    long long n_neg_links = 0, n_neg_stay = 0;
+    std::vector<int32_t> ilist;
+    size_t elem = 4;
+};
+
+namespace {
+
+template <typename T>
+Args<T> make_args(const mp_ctx* c)
+{
+    Args<T> a;
+    memset(&a, 0, sizeof(a));
+    a.nx = c->geo.nx;
+    a.ny = c->geo.ny;
+    a.nz = c->geo.nz;
+    a.N = c->geo.N;
+    a.NI = (int)c->geo.n_iface;
+    a.fluid = c->geo.fluid;
+    a.iface = c->geo.iface;
+    a.ibase = c->geo.ibase;
+    a.u = (const T*)c->u;
+    a.S = c->S;
+    a.F = c->F;
+    a.M = c->M;
+    for (int m = 0; m < 3; ++m) a.dir[m] = c->dir[m];
+    for (int s = 0; s < c->S; ++s) {
+        a.hl[s] = (T)(6.0 * c->Db[s]);  // lambda/2 = 12 D_b / 2
+        a.pa[s] = (T)c->ka[s];
+        a.pd[s] = (T)c->kd[s];
+    }
+    a.partials = c->partials;
+    a.ticket = c->ticket;
+    a.Z = c->Z;
+    a.D = c->D;
+    a.tdev = c->tdev;
+    a.cap = c->cap;
+    return a;
+}
+
+void destroy(mp_ctx* c)
+{
+    if (!c) return;
+    free_geometry(&c->geo, nullptr, false);
+    cudaFree(c->u);
+    for (int b = 0; b < 2; ++b) {
+        cudaFree(c->P[b]);
+        cudaFree(c->A[b]);
+    }
+    cudaFree(c->Z);
+    cudaFree(c->D);
+    cudaFree(c->tdev);
+    cudaFree(c->partials);
+    cudaFree(c->ticket);
+    delete c;
+}
+
+template <typename T>
+int init_typed(mp_ctx* c, const float* u_in, int init_density)
+{
+    const int N = c->geo.N;
+    const size_t NI = (size_t)(c->geo.n_iface > 0 ? c->geo.n_iface : 1);
+    const size_t fieldN = (size_t)c->S * c->F * N;
+    const size_t fieldA = (size_t)c->S * c->F * NI;
+    const int Kser = c->S * c->M;
+    c->elem = sizeof(T);
+    c->blocks = (N + kThreads - 1) / kThreads;
+    MP_CUDA(cudaMalloc(&c->u, sizeof(T) * 3 * (size_t)N));
+    for (int b = 0; b < 2; ++b) {
+        MP_CUDA(cudaMalloc(&c->P[b], sizeof(T) * fieldN));
+        MP_CUDA(cudaMalloc(&c->A[b], sizeof(T) * fieldA));
+        MP_CUDA(cudaMemsetAsync(c->P[b], 0, sizeof(T) * fieldN, c->stream));
+        MP_CUDA(cudaMemsetAsync(c->A[b], 0, sizeof(T) * fieldA, c->stream));
+    }
+    MP_CUDA(cudaMalloc(&c->Z, sizeof(double) * (size_t)Kser * c->cap));
+    MP_CUDA(cudaMalloc(&c->D, sizeof(double) * (size_t)Kser * c->cap));
+    MP_CUDA(cudaMemsetAsync(c->Z, 0, sizeof(double) * (size_t)Kser * c->cap, c->stream));
+    MP_CUDA(cudaMemsetAsync(c->D, 0, sizeof(double) * (size_t)Kser * c->cap, c->stream));
+    MP_CUDA(cudaMalloc(&c->tdev, sizeof(long long)));
+    MP_CUDA(cudaMemsetAsync(c->tdev, 0, sizeof(long long), c->stream));
+    // per-block partials: 2 S M values (initialisation) or 3 (mass check), whichever is more
+    const size_t per_block = (size_t)(2 * Kser > 3 ? 2 * Kser : 3);
+    MP_CUDA(cudaMalloc(&c->partials, sizeof(double) * (size_t)c->blocks * per_block));
+    MP_CUDA(cudaMalloc(&c->ticket, sizeof(unsigned int)));
+    MP_CUDA(cudaMemsetAsync(c->ticket, 0, sizeof(unsigned int), c->stream));
+    k_convert_u<T><<<(3 * N + 255) / 256, 256, 0, c->stream>>>(u_in, (T*)c->u, c->geo.fluid, N);
+    MP_CUDA(cudaGetLastError());
+
+    Args<T> a = make_args<T>(c);
+    // negative link probabilities / stay fractions
+    unsigned long long* counts = nullptr;
+    MP_CUDA(cudaMalloc(&counts, 2 * sizeof(unsigned long long)));
+    cudaMemsetAsync(counts, 0, 2 * sizeof(unsigned long long), c->stream);
+    k_negative<T><<<c->blocks, kThreads, 0, c->stream>>>(a, counts);
+    unsigned long long h_counts[2] = {0, 0};
+    cudaError_t e = cudaGetLastError();
+    if (e == cudaSuccess) e = cudaMemcpyAsync(h_counts, counts, sizeof(h_counts), cudaMemcpyDeviceToHost, c->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
+    cudaFree(counts);
+    if (e != cudaSuccess) return cuda_fail(e, "negative-probability check");
+    c->n_neg_links = (long long)h_counts[0];
+    c->n_neg_stay = (long long)h_counts[1];
+    if (c->n_neg_stay > 0) {
+        set_error("negative stay fraction 1 - sum_i p_i - p_a at " + std::to_string(c->n_neg_stay) +
+                  " node-species (D_b, k_a or |u| too large)");
+        return MP_ENEGPROB;
+    }
+
+    InitExtra b;
+    memset(&b, 0, sizeof(b));
+    for (int s = 0; s < c->S; ++s) {
+        double K = c->ka[s] == 0.0 ? 0.0 : c->ka[s] / c->kd[s];
+        b.K[s] = K;
+        b.invZ[s] = 1.0 / ((double)c->geo.n_fluid + K * (double)c->geo.n_iface);
+    }
+    b.inv_nf = 1.0 / (double)c->geo.n_fluid;
+    b.uniform = init_density == MP_INIT_UNIFORM;
+    k_init<T><<<c->blocks, kThreads, 0, c->stream>>>(a, b, (T*)c->P[0], (T*)c->A[0]);
+    MP_CUDA(cudaGetLastError());
+    c->cur = 0;
+    c->t = 1;
+    return MP_OK;
+}
+
+template <typename T>
+int step_typed(mp_ctx* c, long long n)
+{
+    Args<T> a = make_args<T>(c);
+    for (long long k = 0; k < n; ++k) {
+        const int s = c->cur;
+        k_step<T><<<c->blocks, kThreads, 0, c->stream>>>(a, (const T*)c->P[s], (T*)c->P[1 - s],
+                                                         (const T*)c->A[s], (T*)c->A[1 - s]);
+        c->cur = 1 - s;
+        c->t += 1;
+    }
+    MP_CUDA(cudaGetLastError());
+    return MP_OK;
+}
+
+template <typename T>
+int mass_typed(mp_ctx* c, int sp, double out[3])
+{
+    Args<T> a = make_args<T>(c);
+    const T* P = (const T*)c->P[c->cur] + (size_t)(sp * c->F) * c->geo.N;
+    const size_t NI = (size_t)(c->geo.n_iface > 0 ? c->geo.n_iface : 1);
+    const T* A = (const T*)c->A[c->cur] + (size_t)(sp * c->F) * NI;
+    k_mass<T><<<c->blocks, kThreads, 0, c->stream>>>(a, P, A, c->partials);
+    std::vector<double> h((size_t)c->blocks * 3);
+    MP_CUDA(cudaGetLastError());
+    MP_CUDA(cudaMemcpyAsync(h.data(), c->partials, h.size() * sizeof(double), cudaMemcpyDeviceToHost, c->stream));
+    MP_CUDA(cudaStreamSynchronize(c->stream));
+    out[0] = out[1] = out[2] = 0.0;
+    for (int b = 0; b < c->blocks; ++b)
+        for (int j = 0; j < 3; ++j) out[j] += h[(size_t)b * 3 + j];
+    return MP_OK;
+}
+
+int check_ctx(const mp_ctx* c)
+{
+    if (!c) {
+        set_error("context is NULL");
+        return MP_EINVAL;
+    }
+    return MP_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+void mp_default_options(mp_options* opt)
+{
+    if (!opt) return;
+    memset(opt, 0, sizeof(*opt));
+    opt->precision = MP_FP32;
+    opt->directions = 1;
+    opt->init_density = MP_INIT_EQUILIBRIUM;
+    opt->allow_negative = 0;
+    opt->capacity = 131072;
+    opt->stream = nullptr;
+}
+
+const char* mp_last_error(void) { return mp::last_error_text(); }
+
+int mp_init_batch(mp_ctx** out, const mp_geometry* g, const float* u, int n_species, const double* D_b,
+                  const double* k_a, const double* k_d, const mp_options* opt_in)
+{
+    clear_error();
+    if (!out) {
+        set_error("out is NULL");
+        return MP_EINVAL;
+    }
+    mp_options opt;
+    mp_default_options(&opt);
+    if (opt_in) opt = *opt_in;
+    if (opt.directions == 0) opt.directions = 1;
+    if (opt.capacity == 0) opt.capacity = 131072;
+    if (n_species < 1 || n_species > MP_MAX_SPECIES || !D_b || !k_a || !k_d) {
+        set_error("n_species must be in 1..MP_MAX_SPECIES with non-NULL parameter arrays");
+        return MP_EINVAL;
+    }
+    if (opt.precision != MP_FP32 && opt.precision != MP_FP64) {
+        set_error("precision must be MP_FP32 or MP_FP64");
+        return MP_EINVAL;
+    }
+    if (opt.directions < 1 || opt.directions > 7) {
+        set_error("directions must be a nonzero mask of 1 (x), 2 (y), 4 (z)");
+        return MP_EINVAL;
+    }
+    if (opt.init_density != MP_INIT_EQUILIBRIUM && opt.init_density != MP_INIT_UNIFORM) {
+        set_error("init_density must be MP_INIT_EQUILIBRIUM or MP_INIT_UNIFORM");
+        return MP_EINVAL;
+    }
+    if (opt.capacity < 2 || opt.capacity > (1LL << 40)) {
+        set_error("capacity must be >= 2");
+        return MP_EINVAL;
+    }
+    for (int s = 0; s < n_species; ++s) {
+        if (!(D_b[s] > 0.0 && D_b[s] <= 0.25)) {
+            set_error("D_b must be in (0, 0.25] (lambda = 12 D_b <= 3 keeps the bulk stay >= 0)");
+            return MP_EINVAL;
+        }
+        if (!(k_a[s] >= 0.0 && k_a[s] <= 1.0 && k_d[s] >= 0.0 && k_d[s] <= 1.0)) {
+            set_error("k_a and k_d must be probabilities per step, in [0, 1]");
+            return MP_EINVAL;
+        }
+        if (k_a[s] > 0.0 && k_d[s] == 0.0) {
+            set_error("k_a > 0 with k_d = 0 has no equilibrium (Boltzmann weights need K = k_a/k_d)");
+            return MP_EINVAL;
+        }
+    }
+    mp_ctx* c = new (std::nothrow) mp_ctx();
+    if (!c) {
+        set_error("host allocation failed");
+        return MP_ENOMEM;
+    }
+    c->precision = opt.precision;
+    c->stream = (cudaStream_t)opt.stream;
+    c->cap = opt.capacity;
+    c->S = n_species;
+    c->M = 0;
+    for (int g = 0; g < 3; ++g)
+        if (opt.directions & (1 << g)) c->dir[c->M++] = g;
+    c->F = 1 + c->M;
+    for (int s = 0; s < n_species; ++s) {
+        c->Db[s] = D_b[s];
+        c->ka[s] = k_a[s];
+        c->kd[s] = k_d[s];
+    }
+    int rc = build_geometry(g, c->stream, false, true, &c->geo);
+    if (rc != MP_OK) {
+        delete c;
+        return rc;
+    }
+    if (c->geo.n_fluid == 0) {
+        set_error("the medium has no fluid node");
+        destroy(c);
+        return MP_EINVAL;
+    }
+    if (c->geo.n_iface > 0) {
+        c->ilist.resize((size_t)c->geo.n_iface);
+        cudaError_t e = cudaMemcpyAsync(c->ilist.data(), c->geo.ilist, sizeof(int32_t) * c->ilist.size(),
+                                        cudaMemcpyDeviceToHost, c->stream);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
+        if (e != cudaSuccess) {
+            rc = cuda_fail(e, "interface list copy");
+            destroy(c);
+            return rc;
+        }
+    }
+    rc = c->precision == MP_FP64 ? init_typed<double>(c, u, opt.init_density) : init_typed<float>(c, u, opt.init_density);
+    if (rc == MP_OK && c->n_neg_links > 0 && !opt.allow_negative) {
+        set_error(std::to_string(c->n_neg_links) +
+                  " open links have a negative probability p_i (set allow_negative to accept)");
+        rc = MP_ENEGPROB;
+    }
+    if (rc != MP_OK) {
+        destroy(c);
+        return rc;
+    }
+    *out = c;
+    return MP_OK;
+}
+
+int mp_init(mp_ctx** out, const mp_geometry* g, const float* u, double D_b, double k_a, double k_d,
+            const mp_options* opt)
+{
+    return mp_init_batch(out, g, u, 1, &D_b, &k_a, &k_d, opt);
+}
+
+int mp_step(mp_ctx* c, int64_t n)
+{
+    clear_error();
+    if (int rc = check_ctx(c)) return rc;
+    if (n < 0) {
+        set_error("n must be >= 0");
+        return MP_EINVAL;
+    }
+    if (c->t + n > c->cap - 1) {
+        set_error("the Z/D series is full: capacity " + std::to_string(c->cap) + " time points");
+        return MP_EINVAL;
+    }
+    return c->precision == MP_FP64 ? step_typed<double>(c, n) : step_typed<float>(c, n);
+}
+
+int mp_vacf(mp_ctx* c, int species, int direction, double* Z, double* D, int64_t cap, int64_t* n_out)
+{
+    clear_error();
+    if (int rc = check_ctx(c)) return rc;
+    int m = -1;
+    for (int k = 0; k < c->M; ++k)
+        if (c->dir[k] == direction) m = k;
+    if (species < 0 || species >= c->S || m < 0 || cap < 0) {
+        set_error("species out of range, direction not propagated, or negative cap");
+        return MP_EINVAL;
+    }
+    const long long avail = c->t + 1;
+    const long long cnt = cap < avail ? cap : avail;
+    const size_t off = (size_t)(species * c->M + m) * c->cap;
+    if (cnt > 0 && Z) MP_CUDA(cudaMemcpyAsync(Z, c->Z + off, sizeof(double) * cnt, cudaMemcpyDeviceToHost, c->stream));
+    if (cnt > 0 && D) MP_CUDA(cudaMemcpyAsync(D, c->D + off, sizeof(double) * cnt, cudaMemcpyDeviceToHost, c->stream));
+    MP_CUDA(cudaStreamSynchronize(c->stream));
+    if (n_out) *n_out = avail;
+    return MP_OK;
+}
+
+int mp_mass(mp_ctx* c, int species, double out[3])
+{
+    clear_error();
+    if (int rc = check_ctx(c)) return rc;
+    if (species < 0 || species >= c->S || !out) {
+        set_error("species out of range or out is NULL");
+        return MP_EINVAL;
+    }
+    return c->precision == MP_FP64 ? mass_typed<double>(c, species, out) : mass_typed<float>(c, species, out);
+}
+
+int mp_info(mp_ctx* c, mp_info_t* info)
+{
+    clear_error();
+    if (int rc = check_ctx(c)) return rc;
+    if (!info) {
+        set_error("info is NULL");
+        return MP_EINVAL;
+    }
+    info->n_nodes = c->geo.N;
+    info->n_fluid = c->geo.n_fluid;
+    info->n_interface = c->geo.n_iface;
+    info->n_negative_links = c->n_neg_links;
+    info->t = c->t;
+    info->n_species = c->S;
+    info->n_fields = c->F;
+    info->precision = c->precision;
+    return MP_OK;
+}
+
+int mp_get_field(mp_ctx* c, int species, int field, double* free_dense, double* ads_dense)
+{
+    clear_error();
+    if (int rc = check_ctx(c)) return rc;
+    if (species < 0 || species >= c->S || field < 0 || field >= c->F || !free_dense) {
+        set_error("species or field out of range, or free_dense is NULL");
+        return MP_EINVAL;
+    }
+    const size_t N = (size_t)c->geo.N;
+    const size_t NI = (size_t)(c->geo.n_iface > 0 ? c->geo.n_iface : 1);
+    const size_t fi = (size_t)(species * c->F + field);
+    std::vector<char> buf(N * c->elem), abuf(NI * c->elem);
+    MP_CUDA(cudaMemcpyAsync(buf.data(), (char*)c->P[c->cur] + fi * N * c->elem, N * c->elem, cudaMemcpyDeviceToHost,
+                            c->stream));
+    MP_CUDA(cudaMemcpyAsync(abuf.data(), (char*)c->A[c->cur] + fi * NI * c->elem, NI * c->elem,
+                            cudaMemcpyDeviceToHost, c->stream));
+    MP_CUDA(cudaStreamSynchronize(c->stream));
+    for (size_t n = 0; n < N; ++n)
+        free_dense[n] = c->elem == 8 ? ((double*)buf.data())[n] : (double)((float*)buf.data())[n];
+    if (ads_dense) {
+        for (size_t n = 0; n < N; ++n) ads_dense[n] = 0.0;
+        for (size_t k = 0; k < c->ilist.size(); ++k)
+            ads_dense[c->ilist[k]] = c->elem == 8 ? ((double*)abuf.data())[k] : (double)((float*)abuf.data())[k];
+    }
+    return MP_OK;
+}
+
+int mp_set_field(mp_ctx* c, int species, int field, const double* free_dense, const double* ads_dense)
+{
+    clear_error();
+    if (int rc = check_ctx(c)) return rc;
+    if (species < 0 || species >= c->S || field < 0 || field >= c->F || !free_dense) {
+        set_error("species or field out of range, or free_dense is NULL");
+        return MP_EINVAL;
+    }
+    const size_t N = (size_t)c->geo.N;
+    const size_t NI = (size_t)(c->geo.n_iface > 0 ? c->geo.n_iface : 1);
+    const size_t fi = (size_t)(species * c->F + field);
+    // solid nodes stay zero: read the fluid bits back to mask them
+    std::vector<uint32_t> fl((size_t)c->geo.W);
+    MP_CUDA(cudaMemcpyAsync(fl.data(), c->geo.fluid, fl.size() * 4, cudaMemcpyDeviceToHost, c->stream));
+    MP_CUDA(cudaStreamSynchronize(c->stream));
+    std::vector<char> buf(N * c->elem), abuf(NI * c->elem, 0);
+    for (size_t n = 0; n < N; ++n) {
+        const bool f = (fl[n >> 5] >> (n & 31)) & 1u;
+        const double v = f ? free_dense[n] : 0.0;
+        if (c->elem == 8)
+            ((double*)buf.data())[n] = v;
+        else
+            ((float*)buf.data())[n] = (float)v;
+    }
+    for (size_t k = 0; k < c->ilist.size(); ++k) {
+        const double v = ads_dense ? ads_dense[c->ilist[k]] : 0.0;
+        if (c->elem == 8)
+            ((double*)abuf.data())[k] = v;
+        else
+            ((float*)abuf.data())[k] = (float)v;
+    }
+    MP_CUDA(cudaMemcpyAsync((char*)c->P[c->cur] + fi * N * c->elem, buf.data(), N * c->elem, cudaMemcpyHostToDevice,
+                            c->stream));
+    MP_CUDA(cudaMemcpyAsync((char*)c->A[c->cur] + fi * NI * c->elem, abuf.data(), NI * c->elem,
+                            cudaMemcpyHostToDevice, c->stream));
+    MP_CUDA(cudaStreamSynchronize(c->stream));
+    return MP_OK;
+}
+
+void mp_free(mp_ctx* c)
+{
+    if (!c) return;
+    if (c->stream) cudaStreamSynchronize(c->stream);
+    destroy(c);
+}
+
+}  // extern "C"

@@ -1,0 +1,257 @@
+"""Thin Python binding of libmp (the C ABI in include/mp.h), with the same entry-point
+names. It only marshals arguments: every step of the computation runs in the CUDA library.
+
+Device buffers are passed as objects with a ``data_ptr()`` method (torch CUDA tensors) or
+as integer addresses; host arrays are numpy arrays. Importing this module loads
+``libmp.so`` and raises ImportError when it has not been built, so there is no silent
+fallback to any other implementation.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libmp.so")
+if not os.path.exists(LIB_PATH):
+    raise ImportError(f"{LIB_PATH} is not built: run paper_1303_2470_gb300.build.build() "
+                      "(or __graft_entry__.build()) on a machine with the CUDA toolkit")
+_lib = ctypes.CDLL(LIB_PATH)
+
+MP_OK = 0
+MP_EINVAL = -1
+MP_ENOMEM = -2
+MP_ECUDA = -3
+MP_ENEGPROB = -4
+MP_ENOTCONVERGED = -5
+MP_ETIMEOUT = -6
+MP_HOST = 0
+MP_DEVICE = 1
+MP_FP32 = 0
+MP_FP64 = 1
+MP_INIT_EQUILIBRIUM = 0
+MP_INIT_UNIFORM = 1
+MP_MAX_SPECIES = 32
+
+_c_int, _c_i64, _c_dbl, _c_vp = ctypes.c_int, ctypes.c_int64, ctypes.c_double, ctypes.c_void_p
+
+
+class mp_geometry(ctypes.Structure):
+    _fields_ = [("nx", _c_int), ("ny", _c_int), ("nz", _c_int), ("solid", _c_vp), ("location", _c_int)]
+
+
+class mp_options(ctypes.Structure):
+    _fields_ = [("precision", _c_int), ("directions", _c_int), ("init_density", _c_int),
+                ("allow_negative", _c_int), ("capacity", _c_i64), ("stream", _c_vp)]
+
+
+class mp_info_t(ctypes.Structure):
+    _fields_ = [("n_nodes", _c_i64), ("n_fluid", _c_i64), ("n_interface", _c_i64),
+                ("n_negative_links", _c_i64), ("t", _c_i64), ("n_species", _c_int),
+                ("n_fields", _c_int), ("precision", _c_int)]
+
+
+_dp = ctypes.POINTER(_c_dbl)
+_lib.mp_default_options.argtypes = [ctypes.POINTER(mp_options)]
+_lib.mp_default_options.restype = None
+_lib.mp_last_error.restype = ctypes.c_char_p
+_lib.mp_init.argtypes = [ctypes.POINTER(_c_vp), ctypes.POINTER(mp_geometry), _c_vp, _c_dbl, _c_dbl,
+                         _c_dbl, ctypes.POINTER(mp_options)]
+_lib.mp_init_batch.argtypes = [ctypes.POINTER(_c_vp), ctypes.POINTER(mp_geometry), _c_vp, _c_int,
+                               _dp, _dp, _dp, ctypes.POINTER(mp_options)]
+_lib.mp_step.argtypes = [_c_vp, _c_i64]
+_lib.mp_vacf.argtypes = [_c_vp, _c_int, _c_int, _dp, _dp, _c_i64, ctypes.POINTER(_c_i64)]
+_lib.mp_mass.argtypes = [_c_vp, _c_int, _dp]
+_lib.mp_info.argtypes = [_c_vp, ctypes.POINTER(mp_info_t)]
+_lib.mp_get_field.argtypes = [_c_vp, _c_int, _c_int, _dp, _dp]
+_lib.mp_set_field.argtypes = [_c_vp, _c_int, _c_int, _dp, _dp]
+_lib.mp_free.argtypes = [_c_vp]
+_lib.mp_free.restype = None
+_lib.lb_steady.argtypes = [ctypes.POINTER(mp_geometry), _dp, _c_dbl, _c_dbl, _c_i64, _c_i64, _c_vp,
+                           _c_vp, ctypes.POINTER(_c_i64), _dp, _c_vp]
+for _f in ("mp_init", "mp_init_batch", "mp_step", "mp_vacf", "mp_mass", "mp_info", "mp_get_field",
+           "mp_set_field", "lb_steady"):
+    getattr(_lib, _f).restype = _c_int
+
+
+class MPError(RuntimeError):
+    def __init__(self, code, msg):
+        super().__init__(f"libmp status {code}: {msg}")
+        self.code = code
+
+
+def mp_last_error() -> str:
+    return _lib.mp_last_error().decode()
+
+
+def _check(rc):
+    if rc != MP_OK:
+        raise MPError(rc, mp_last_error())
+    return rc
+
+
+def _addr(buf):
+    """Device address of a torch tensor / object with data_ptr(), or an int; None -> NULL."""
+    if buf is None:
+        return None
+    if hasattr(buf, "data_ptr"):
+        return int(buf.data_ptr())
+    return int(buf)
+
+
+def _stream(stream):
+    if stream is None:
+        return None
+    if hasattr(stream, "cuda_stream"):
+        return int(stream.cuda_stream)
+    return int(stream)
+
+
+def make_geometry(solid):
+    """mp_geometry for a solid mask: a numpy (host) or CUDA tensor (device) uint8 array
+    shaped (nz, ny, nx). Returns (struct, keep-alive object)."""
+    if hasattr(solid, "data_ptr") and getattr(solid, "is_cuda", False):
+        assert solid.dtype.itemsize == 1 if hasattr(solid.dtype, "itemsize") else True
+        nz, ny, nx = solid.shape
+        t = solid.contiguous()
+        return mp_geometry(nx, ny, nz, t.data_ptr(), MP_DEVICE), t
+    a = np.ascontiguousarray(solid, dtype=np.uint8)
+    nz, ny, nx = a.shape
+    return mp_geometry(nx, ny, nz, a.ctypes.data, MP_HOST), a
+
+
+def mp_default_options() -> mp_options:
+    o = mp_options()
+    _lib.mp_default_options(ctypes.byref(o))
+    return o
+
+
+def _options(precision="fp32", directions="x", init_density="equilibrium", allow_negative=False,
+             capacity=0, stream=None):
+    o = mp_default_options()
+    o.precision = {"fp32": MP_FP32, "fp64": MP_FP64}[precision]
+    o.directions = sum({"x": 1, "y": 2, "z": 4}[d] for d in directions)
+    o.init_density = {"equilibrium": MP_INIT_EQUILIBRIUM, "uniform": MP_INIT_UNIFORM}[init_density]
+    o.allow_negative = int(bool(allow_negative))
+    o.capacity = int(capacity)
+    o.stream = _stream(stream)
+    return o
+
+
+class Context:
+    """Owning handle of an mp_ctx*; mp_free() runs on close() or garbage collection."""
+
+    def __init__(self, ptr, shape, directions):
+        self.ptr = ptr
+        self.shape = shape
+        self.directions = directions
+
+    def close(self):
+        if self.ptr:
+            _lib.mp_free(self.ptr)
+            self.ptr = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def mp_init(solid, u, D_b, k_a, k_d, **options) -> Context:
+    """mp_init of include/mp.h. solid: host numpy or device tensor (nz,ny,nx) uint8;
+    u: device FP32 buffer of 3*N values (SoA) or None. Options: precision ("fp32"/"fp64"),
+    directions (e.g. "x", "xz"), init_density ("equilibrium"/"uniform"), allow_negative,
+    capacity, stream."""
+    return mp_init_batch(solid, u, [D_b], [k_a], [k_d], **options)
+
+
+def mp_init_batch(solid, u, D_b, k_a, k_d, **options) -> Context:
+    g, keep = make_geometry(solid)
+    Db = np.ascontiguousarray(D_b, dtype=np.float64)
+    ka = np.ascontiguousarray(k_a, dtype=np.float64)
+    kd = np.ascontiguousarray(k_d, dtype=np.float64)
+    if not (Db.shape == ka.shape == kd.shape and Db.ndim == 1):
+        raise ValueError("D_b, k_a, k_d must be 1-D arrays of equal length")
+    o = _options(**options)
+    out = _c_vp()
+    _check(_lib.mp_init_batch(ctypes.byref(out), ctypes.byref(g), _addr(u), len(Db),
+                              Db.ctypes.data_as(_dp), ka.ctypes.data_as(_dp), kd.ctypes.data_as(_dp),
+                              ctypes.byref(o)))
+    del keep
+    return Context(out, (g.nz, g.ny, g.nx), options.get("directions", "x"))
+
+
+def mp_step(ctx: Context, n: int):
+    _check(_lib.mp_step(ctx.ptr, int(n)))
+
+
+def mp_vacf(ctx: Context, species: int = 0, direction: int = 0, cap: int | None = None):
+    """Returns (Z, D), numpy float64 arrays of the available time points (t = 0..T)."""
+    n = _c_i64()
+    _check(_lib.mp_vacf(ctx.ptr, species, direction, None, None, 0, ctypes.byref(n)))
+    T = n.value if cap is None else min(n.value, cap)
+    Z = np.zeros(T)
+    D = np.zeros(T)
+    _check(_lib.mp_vacf(ctx.ptr, species, direction, Z.ctypes.data_as(_dp), D.ctypes.data_as(_dp), T,
+                        ctypes.byref(n)))
+    return Z, D
+
+
+def mp_vacf_into(ctx: Context, species: int, direction: int, Z: np.ndarray, D: np.ndarray) -> int:
+    """mp_vacf into caller-owned host arrays (e.g. pinned); returns the time points available."""
+    n = _c_i64()
+    _check(_lib.mp_vacf(ctx.ptr, species, direction, Z.ctypes.data_as(_dp), D.ctypes.data_as(_dp),
+                        min(Z.size, D.size), ctypes.byref(n)))
+    return n.value
+
+
+def mp_mass(ctx: Context, species: int = 0) -> np.ndarray:
+    out = np.zeros(3)
+    _check(_lib.mp_mass(ctx.ptr, species, out.ctypes.data_as(_dp)))
+    return out
+
+
+def mp_info(ctx: Context) -> dict:
+    i = mp_info_t()
+    _check(_lib.mp_info(ctx.ptr, ctypes.byref(i)))
+    return {k: getattr(i, k) for k, _ in mp_info_t._fields_}
+
+
+def mp_get_field(ctx: Context, species: int = 0, field: int = 0):
+    """(free, adsorbed) dense float64 arrays shaped (nz, ny, nx)."""
+    fr = np.zeros(ctx.shape)
+    ad = np.zeros(ctx.shape)
+    _check(_lib.mp_get_field(ctx.ptr, species, field, fr.ctypes.data_as(_dp), ad.ctypes.data_as(_dp)))
+    return fr, ad
+
+
+def mp_set_field(ctx: Context, species: int, field: int, free, ads=None):
+    fr = np.ascontiguousarray(free, dtype=np.float64)
+    ad = None if ads is None else np.ascontiguousarray(ads, dtype=np.float64)
+    _check(_lib.mp_set_field(ctx.ptr, species, field, fr.ctypes.data_as(_dp),
+                             ad.ctypes.data_as(_dp) if ad is not None else None))
+
+
+def mp_free(ctx: Context):
+    ctx.close()
+
+
+def lb_steady(solid, force, u_out, tau=1.0, tol=1e-7, max_steps=1_000_000, check_every=100,
+              u_init=None, stream=None, raise_on_unconverged=False):
+    """lb_steady of include/mp.h; u_out (and u_init) are device FP32 buffers of 3*N values.
+    Returns (steps, residual, converged)."""
+    g, keep = make_geometry(solid)
+    F = np.ascontiguousarray(force, dtype=np.float64)
+    steps = _c_i64()
+    res = _c_dbl()
+    rc = _lib.lb_steady(ctypes.byref(g), F.ctypes.data_as(_dp), float(tau), float(tol), int(max_steps),
+                        int(check_every), _addr(u_init), _addr(u_out), ctypes.byref(steps),
+                        ctypes.byref(res), _stream(stream))
+    del keep
+    if rc == MP_ENOTCONVERGED and not raise_on_unconverged:
+        return steps.value, res.value, False
+    _check(rc)
+    return steps.value, res.value, True

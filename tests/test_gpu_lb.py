@@ -1,0 +1,111 @@
+"""GPU parity of lb_steady (through the C ABI) against the FP64 oracle LB, and the slit
+Poiseuille + sorption pipeline (LB flow feeding the moment propagation) against the oracle.
+
+FP32 populations against the FP64 oracle: velocities within 1e-4 of the largest speed
+after a fixed number of steps (the same steps on both sides, tol = 0)."""
+import numpy as np
+import pytest
+
+import oracle
+from paper_1303_2470_gb300 import media
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def mp():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_1303_2470_gb300 import build
+    build.build()
+    from paper_1303_2470_gb300 import mp as m
+    return m
+
+
+def _u_dev(shape):
+    return torch.zeros((3,) + tuple(shape), dtype=torch.float32, device="cuda")
+
+
+def test_fixed_steps_porous_medium(mp):
+    """Ragged 23x26x19 random medium, body force in two directions, tau = 0.8: u after 400
+    steps agrees with the oracle's."""
+    solid, _ = media.random_spheres((19, 26, 23), 3, 0.55, seed=5)
+    F = (2e-5, -1e-5, 0.5e-5)
+    u = _u_dev(solid.shape)
+    steps, res, conv = mp.lb_steady(solid, F, u, tau=0.8, tol=0.0, max_steps=400, check_every=50)
+    assert steps == 400 and not conv
+    uo, so, ro, co = oracle.lb_steady(solid, F, tau=0.8, tol=0.0, max_steps=400, check_every=50)
+    ug = u.cpu().numpy().astype(np.float64)
+    scale = np.abs(uo).max()
+    assert np.max(np.abs(ug - uo)) < 1e-4 * scale
+    assert abs(res - ro) < 1e-3 * ro + 1e-12
+    assert np.all(ug[:, solid.astype(bool)] == 0.0)
+
+
+def test_rest_stays_at_rest(mp):
+    solid, _ = media.random_spheres((16, 16, 16), 3, 0.6, seed=2)
+    u = _u_dev(solid.shape)
+    steps, res, conv = mp.lb_steady(solid, (0, 0, 0), u, tol=1e-12, max_steps=50, check_every=10)
+    assert conv and steps == 10 and res == 0.0
+    assert float(u.abs().max()) == 0.0
+
+
+def test_slit_poiseuille_steady_state(mp):
+    """Slit H = 32, tau = 1, F = 8 nu u_max / H^2 (u_max = 0.05): converges below 1e-7 within
+    a check period of the oracle, and the profiles agree."""
+    H = 32
+    F = 8 * (1.0 / 6.0) * 0.05 / H ** 2
+    solid = media.slit(16, 16, H)
+    u = _u_dev(solid.shape)
+    steps, res, conv = mp.lb_steady(solid, (F, 0, 0), u, tol=1e-7, max_steps=200_000, check_every=100)
+    uo, so, ro, co = oracle.lb_steady(media.slit(3, 3, H), (F, 0, 0), tol=1e-7, max_steps=200_000,
+                                      check_every=100)
+    assert conv and co and res < 1e-7
+    assert abs(steps - so) <= 200
+    ug = u.cpu().numpy()[0, :, 7, 5].astype(np.float64)
+    assert np.max(np.abs(ug - uo[0, :, 1, 1])) < 2e-4 * 0.05
+    assert np.all(u.cpu().numpy()[0] == u.cpu().numpy()[0, :, :1, :1])   # x,y invariant
+    assert abs(ug.max() - 0.05) < 2e-3
+
+
+def test_not_converged_status_and_warm_start(mp):
+    H = 16
+    F = 8 * (1.0 / 6.0) * 0.05 / H ** 2
+    solid = media.slit(8, 8, H)
+    u = _u_dev(solid.shape)
+    steps, res, conv = mp.lb_steady(solid, (F, 0, 0), u, tol=1e-7, max_steps=300, check_every=100)
+    assert not conv and steps == 300 and res > 1e-7
+    with pytest.raises(mp.MPError) as e:
+        mp.lb_steady(solid, (F, 0, 0), u, tol=1e-7, max_steps=300, check_every=100,
+                     raise_on_unconverged=True)
+    assert e.value.code == mp.MP_ENOTCONVERGED
+    cold = mp.lb_steady(solid, (F, 0, 0), u, tol=1e-7, max_steps=100_000, check_every=100)
+    u2 = _u_dev(solid.shape)
+    warm = mp.lb_steady(solid, (F, 0, 0), u2, tol=1e-7, max_steps=100_000, check_every=100, u_init=u)
+    assert cold[2] and warm[2] and warm[0] < cold[0]
+
+
+@pytest.mark.parametrize("ka,kd", [(0.0, 0.0), (1e-3, 1e-2), (1e-2, 1e-3)])
+def test_poiseuille_sorption_pipeline(mp, ka, kd):
+    """Slit Poiseuille flow with sorption: 16x16 periodic, H = 32, BGK tau = 1 to 1e-7, MP with
+    D_b = 0.02 and 5e4 FP32 steps. The slit is x,y-invariant, so the oracle runs the same
+    flow profile on a 3x3 cross-section (Z and D do not depend on it)."""
+    H, steps = 32, 50_000
+    F = 8 * (1.0 / 6.0) * 0.05 / H ** 2
+    solid = media.slit(16, 16, H)
+    u = _u_dev(solid.shape)
+    _, _, conv = mp.lb_steady(solid, (F, 0, 0), u, tol=1e-7, max_steps=200_000, check_every=100)
+    assert conv
+    ctx = mp.mp_init(solid, u, 0.02, ka, kd, capacity=steps + 2)
+    mp.mp_step(ctx, steps)
+    Z, D = mp.mp_vacf(ctx, 0, 0)
+    prof = u.cpu().numpy()[:, :, 0, 0].astype(np.float64)
+    small = media.slit(3, 3, H)
+    uo = np.broadcast_to(prof[:, :, None, None], (3,) + small.shape).copy()
+    ref = oracle.run(oracle.Problem(small, uo, 0.02, ka, kd), g=0, nsteps=steps)
+    assert np.max(np.abs(Z - ref.Z)) / abs(ref.Z[0]) < 1e-4
+    assert np.max(np.abs(D - ref.D) / np.abs(ref.D)) < 1e-4
+    m = mp.mp_mass(ctx, 0)
+    assert abs(m[0] + m[1] - 1.0) < 1e-4
+    ctx.close()
