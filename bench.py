@@ -250,7 +250,7 @@ def main():
                                         stream=stream)
         ev[1].record(stream)
         ctx = mp.mp_init(solid_arg, u, WORKLOAD["D_b"], WORKLOAD["k_a"], WORKLOAD["k_d"],
-                         capacity=WORKLOAD["mp_steps"] + 2, stream=stream)
+                         capacity=WORKLOAD["mp_steps"] + 2, stream=stream, allow_negative=True)
         ev[2].record(stream)
         mp.mp_step(ctx, WORKLOAD["mp_steps"])
         if host_out is not None:
@@ -341,6 +341,7 @@ def main():
         "warmup": args.warmup, "ms_per_step": total_ms_max / args.steps, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
         "config": dict(WORKLOAD, n_fluid=n_fluid, n_interface=n_iface, spheres=nspheres,
+                       negative_links=int(info["n_negative_links"]),
                        force_x=Fx, l2="256 MiB buffer written between timed jobs",
                        parallelism="replicas" if world > 1 else "single GPU"),
         "lb": {"steps_to_steady": lb_steps_all, "ms": lb_ms / args.steps,

@@ -64,66 +64,80 @@ __device__ __forceinline__ bool bit_of(const uint32_t* __restrict__ w, int n)
 }
 __device__ __forceinline__ int wrap(int v, int n) { return v < 0 ? v + n : (v >= n ? v - n : v); }
 
-// What a fluid node needs from its own links and its 18 upstream neighbours.
-template <typename T>
-struct Node {
-    T coef[kQ];   // advective part of p_i at the source r - c_i (i >= 1)
-    int src[kQ];  // source node r - c_i, -1 when it is solid (no inflow on that link)
-    T SA, SW;     // sum over open links of w_i adv_i(r), of w_i
-    T UA[3], UW[3];  // sum over open links of w_i adv_i(r) c_ig, of w_i c_ig
-    T QA[3], QW[3];  // same with c_ig^2 (Z(0) only)
-    bool itf;
-    int aidx;  // compact index among interfacial nodes
-};
+// Correctly rounded arithmetic the compiler may not contract or reorder. A link
+// probability is evaluated by both end nodes of the link and must come out bitwise equal,
+// so that the two ends compute exactly opposite net fluxes (the step conserves mass up to
+// the final, unbiased rounding of each node's update).
+__device__ __forceinline__ float rn_mul(float a, float b) { return __fmul_rn(a, b); }
+__device__ __forceinline__ float rn_add(float a, float b) { return __fadd_rn(a, b); }
+__device__ __forceinline__ float rn_sub(float a, float b) { return __fsub_rn(a, b); }
+__device__ __forceinline__ double rn_mul(double a, double b) { return __dmul_rn(a, b); }
+__device__ __forceinline__ double rn_add(double a, double b) { return __dadd_rn(a, b); }
+__device__ __forceinline__ double rn_sub(double a, double b) { return __dsub_rn(a, b); }
 
+template <typename T>
+__device__ __forceinline__ T speed2(T ux, T uy, T uz)
+{
+    return rn_add(rn_add(rn_mul(ux, ux), rn_mul(uy, uy)), rn_mul(uz, uz));
+}
+
+// Advective part of the link probability, w_i (3 e + 9/2 e^2 - 3/2 |u|^2), e = c_i.u
+// (f_i^eq(rho = 1, u)/rho - w_i), in a fixed sequence of correctly rounded operations.
 template <typename T>
 __device__ __forceinline__ T advective(int i, T ux, T uy, T uz, T uu)
 {
-    T e = T(cx(i)) * ux + T(cy(i)) * uy + T(cz(i)) * uz;
-    return weight<T>(i) * (T(3) * e + T(4.5) * e * e - T(1.5) * uu);
+    const T e = rn_add(rn_add(rn_mul(T(cx(i)), ux), rn_mul(T(cy(i)), uy)), rn_mul(T(cz(i)), uz));
+    const T q = rn_sub(rn_add(rn_mul(T(3), e), rn_mul(T(4.5), rn_mul(e, e))), rn_mul(T(1.5), uu));
+    return rn_mul(weight<T>(i), q);
 }
+
+// What a fluid node r needs from its links. Link i is the inflow direction c_i: its source
+// is s_i = r - c_i, and the reverse link (opposite(i), from r to s_i) carries the outflow.
+// Both are open iff s_i is fluid.
+template <typename T>
+struct Node {
+    T cin[kQ];       // advective part of p_i at s_i (link s_i -> r)
+    T cout[kQ];      // advective part of p_opposite(i) at r (link r -> s_i)
+    int src[kQ];     // s_i, or -1 when s_i is solid
+    T UA[3], UW[3];  // sum over open outgoing links of w adv c_g, of w c_g  (u*_g)
+    T QA[3], QW[3];  // same with c_g^2 (Z(0) only)
+    bool itf;
+    int aidx;  // compact index among interfacial nodes
+};
 
 template <typename T, bool kWithQ>
 __device__ __forceinline__ void load_node(const Args<T>& a, int n, Node<T>& d)
 {
     const int x = n % a.nx, y = (n / a.nx) % a.ny, z = n / (a.nx * a.ny);
     const T ux = a.u[n], uy = a.u[a.N + n], uz = a.u[2 * a.N + n];
-    const T uu = ux * ux + uy * uy + uz * uz;
-    d.SA = d.SW = T(0);
+    const T uu = speed2(ux, uy, uz);
 #pragma unroll
     for (int g = 0; g < 3; ++g) d.UA[g] = d.UW[g] = d.QA[g] = d.QW[g] = T(0);
     d.itf = false;
 #pragma unroll
     for (int i = 1; i < kQ; ++i) {
-        // outgoing link: open iff r + c_i is fluid
-        const int t = wrap(x + cx(i), a.nx) + a.nx * (wrap(y + cy(i), a.ny) + a.ny * wrap(z + cz(i), a.nz));
-        if (bit_of(a.fluid, t)) {
-            const T ad = advective<T>(i, ux, uy, uz, uu);
-            d.SA += ad;
-            d.SW += weight<T>(i);
+        const int s = wrap(x - cx(i), a.nx) + a.nx * (wrap(y - cy(i), a.ny) + a.ny * wrap(z - cz(i), a.nz));
+        const int o = opposite(i);
+        if (bit_of(a.fluid, s)) {
+            const T sx = a.u[s], sy = a.u[a.N + s], sz = a.u[2 * a.N + s];
+            d.cin[i] = advective<T>(i, sx, sy, sz, speed2(sx, sy, sz));
+            d.cout[i] = advective<T>(o, ux, uy, uz, uu);
+            d.src[i] = s;
 #pragma unroll
             for (int g = 0; g < 3; ++g) {
-                if (ci(i, g) != 0) {
-                    d.UA[g] += ad * T(ci(i, g));
-                    d.UW[g] += weight<T>(i) * T(ci(i, g));
+                if (ci(o, g) != 0) {
+                    d.UA[g] += d.cout[i] * T(ci(o, g));
+                    d.UW[g] += weight<T>(o) * T(ci(o, g));
                     if (kWithQ) {
-                        d.QA[g] += ad;
-                        d.QW[g] += weight<T>(i);
+                        d.QA[g] += d.cout[i];
+                        d.QW[g] += weight<T>(o);
                     }
                 }
             }
         } else {
-            d.itf = true;
-        }
-        // incoming link: from s = r - c_i
-        const int s = wrap(x - cx(i), a.nx) + a.nx * (wrap(y - cy(i), a.ny) + a.ny * wrap(z - cz(i), a.nz));
-        if (bit_of(a.fluid, s)) {
-            const T sx = a.u[s], sy = a.u[a.N + s], sz = a.u[2 * a.N + s];
-            d.coef[i] = advective<T>(i, sx, sy, sz, sx * sx + sy * sy + sz * sz);
-            d.src[i] = s;
-        } else {
-            d.coef[i] = T(0);
+            d.cin[i] = d.cout[i] = T(0);
             d.src[i] = -1;
+            d.itf = true;
         }
     }
     d.aidx = 0;
@@ -218,24 +232,37 @@ __global__ void __launch_bounds__(kThreads)
         const T hl = a.hl[sp], pa = a.pa[sp], pd = a.pd[sp];
         T zp[kMaxF] = {T(0), T(0), T(0), T(0)};
         if (active) {
-            const T stay = T(1) - d.SA - hl * d.SW - (d.itf ? pa : T(0));
+            // link probabilities of this species: p = advective part + w lambda/2
+            const T whl_face = rn_mul(weight<T>(1), hl), whl_edge = rn_mul(weight<T>(5), hl);
+            T pin[kQ], pout[kQ];
+#pragma unroll
+            for (int i = 1; i < kQ; ++i) {
+                const T whl = is_face(i) ? whl_face : whl_edge;
+                pin[i] = rn_add(d.cin[i], whl);
+                pout[i] = rn_add(d.cout[i], whl);
+            }
 #pragma unroll
             for (int f = 0; f < kMaxF; ++f) {
                 if (f < a.F) {
                     const size_t base = (size_t)(sp * a.F + f) * a.N;
                     const T* X = P + base;
-                    T acc = T(0);
+                    const T xr = __ldg(X + n);
+                    // Eq. propagated_quantity as a sum of net link fluxes
+                    // J_i = p_i(s_i) X(s_i) - p_opp(i)(r) X(r): the stay fraction never appears
+                    T delta = T(0);
 #pragma unroll
                     for (int i = 1; i < kQ; ++i)
-                        if (d.src[i] >= 0) acc += (d.coef[i] + weight<T>(i) * hl) * __ldg(X + d.src[i]);
-                    const T xr = __ldg(X + n);
-                    T xn = acc + stay * xr;
+                        if (d.src[i] >= 0)
+                            delta = rn_add(delta, rn_sub(rn_mul(pin[i], __ldg(X + d.src[i])), rn_mul(pout[i], xr)));
                     if (d.itf) {
+                        // Eqs. Pads, newP: exchange J_s = p_a X - p_d X_ads
                         const size_t ai = (size_t)(sp * a.F + f) * a.NI + d.aidx;
                         const T xa = A[ai];
-                        xn += pd * xa;
-                        An[ai] = pa * xr + (T(1) - pd) * xa;
+                        const T js = rn_sub(rn_mul(pa, xr), rn_mul(pd, xa));
+                        delta = rn_sub(delta, js);
+                        An[ai] = rn_add(xa, js);
                     }
+                    const T xn = rn_add(xr, delta);
                     Pn[base + n] = xn;
                     if (f >= 1) {
                         const int g = a.dir[f - 1];
@@ -280,7 +307,11 @@ __global__ void __launch_bounds__(kThreads)
         const T invZ = (T)b.invZ[sp];
         T zp[2 * kMaxF] = {T(0), T(0), T(0), T(0), T(0), T(0), T(0), T(0)};
         if (active) {
-            const T stay = T(1) - d.SA - hl * d.SW - (d.itf ? pa : T(0));
+            T out = T(0);
+#pragma unroll
+            for (int i = 1; i < kQ; ++i)
+                if (d.src[i] >= 0) out += d.cout[i] + weight<T>(i) * hl;
+            const T stay = T(1) - out - (d.itf ? pa : T(0));
             // density field: X0 uniform over the free fluid (1/N_f or the free weight 1/Z),
             // adsorbed K/Z on the interface for the equilibrium start
             const T x0 = b.uniform ? (T)b.inv_nf : invZ;
@@ -288,7 +319,7 @@ __global__ void __launch_bounds__(kThreads)
             T inflow = T(0);
 #pragma unroll
             for (int i = 1; i < kQ; ++i)
-                if (d.src[i] >= 0) inflow += (d.coef[i] + weight<T>(i) * hl) * x0;
+                if (d.src[i] >= 0) inflow += (d.cin[i] + weight<T>(i) * hl) * x0;
             T xn = inflow + stay * x0;
             if (d.itf) {
                 const size_t ai = (size_t)(sp * a.F) * a.NI + d.aidx;
@@ -304,7 +335,7 @@ __global__ void __launch_bounds__(kThreads)
 #pragma unroll
                     for (int i = 1; i < kQ; ++i)
                         if (d.src[i] >= 0 && ci(i, g) != 0)
-                            pg += (d.coef[i] + weight<T>(i) * hl) * T(ci(i, g)) * invZ;
+                            pg += (d.cin[i] + weight<T>(i) * hl) * T(ci(i, g)) * invZ;
                     P1[(size_t)(sp * a.F + 1 + m) * a.N + n] = pg;
                     if (d.itf) A1[(size_t)(sp * a.F + 1 + m) * a.NI + d.aidx] = T(0);
                     zp[2 * m] = invZ * (pick(d.QA, g) + hl * pick(d.QW, g));
