@@ -166,6 +166,23 @@ int mp_get_field(mp_ctx* c, int species, int field, double* free_dense, double* 
 int mp_set_field(mp_ctx* c, int species, int field, const double* free_dense,
                  const double* ads_dense);
 
+/*
+ * mp_classify -- node classes of a medium, as used by every other entry point.
+ *
+ * Paper: Sec. "Algorithm", the three node classes of the Boltzmann weights: solid S, fluid F
+ * and interfacial I (fluid nodes with at least one solid D3Q19 neighbour). Also marks the
+ * largest cluster of fluid nodes connected by D3Q19 links (periodic), on which lb_steady
+ * applies its body force (ties go to the cluster holding the smallest node index).
+ *  g            the medium (host or device mask).
+ *  cls          host, N bytes out: 0 solid, 1 fluid, 2 interfacial, plus 4 when the node is
+ *               in the largest cluster.
+ *  n_fluid, n_interface, n_cluster   host outputs (each may be NULL).
+ *  stream       cudaStream_t or NULL; synchronised before return.
+ * Errors: MP_EINVAL, MP_ENOMEM, MP_ECUDA.
+ */
+int mp_classify(const mp_geometry* g, uint8_t* cls, int64_t* n_fluid, int64_t* n_interface,
+                int64_t* n_cluster, void* stream);
+
 /* mp_free -- release a context and all its device memory (NULL is accepted). */
 void mp_free(mp_ctx* c);
 
@@ -179,6 +196,8 @@ const char* mp_last_error(void);
  * collision Delta_i = -(f_i - f_i^eq)/tau, the Guo body-force term for a uniform force F on
  * fluid nodes, u = (sum_i f_i c_i + F/2)/rho, and halfway bounce-back on links into solid
  * nodes. Populations are stored in FP32 as deviations f_i - w_i; the residual is FP64.
+ * The force acts on the largest connected fluid cluster only (see mp_classify): a uniform
+ * force in a sealed pocket is balanced by pressure, so its steady velocity is zero there.
  *
  *  g             the medium (host or device mask; copied for the call).
  *  force         host, 3 doubles: body force per node.

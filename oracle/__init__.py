@@ -215,21 +215,35 @@ def lb_init(solid: np.ndarray, u0: np.ndarray | None = None) -> np.ndarray:
     return f
 
 
-def lb_step(solid, f, force, tau=1.0):
-    """One BGK + Guo + halfway bounce-back step; returns (f', u[3,nz,ny,nx])."""
+def largest_cluster(solid):
+    """(in_cluster uint8[...], size): the largest D3Q19-connected cluster of fluid nodes."""
+    s = np.ascontiguousarray(solid, dtype=np.uint8)
+    nz, ny, nx = s.shape
+    out = np.zeros_like(s)
+    size = ctypes.c_int64()
+    if _load().or_largest_cluster(nx, ny, nz, _ptr(s, _u8p), _ptr(out, _u8p), ctypes.byref(size)) != 0:
+        raise MemoryError("oracle cluster search")
+    return out, size.value
+
+
+def lb_step(solid, f, force, tau=1.0, forced=None):
+    """One BGK + Guo + halfway bounce-back step; returns (f', u[3,nz,ny,nx]). The force
+    acts where `forced` is nonzero (on every fluid node when None)."""
     s = np.ascontiguousarray(solid, dtype=np.uint8)
     nz, ny, nx = s.shape
     f = np.ascontiguousarray(f, dtype=np.float64)
     fo = np.zeros_like(f)
     u = np.zeros((3,) + s.shape)
     F = (ctypes.c_double * 3)(*[float(v) for v in force])
-    _load().or_lb_step(nx, ny, nz, _ptr(s, _u8p), F, ctypes.c_double(tau), _ptr(f, _dp),
-                       _ptr(fo, _dp), _ptr(u, _dp))
+    fm = None if forced is None else np.ascontiguousarray(forced, dtype=np.uint8)
+    _load().or_lb_step(nx, ny, nz, _ptr(s, _u8p), _ptr(fm, _u8p) if fm is not None else _u8p(), F,
+                       ctypes.c_double(tau), _ptr(f, _dp), _ptr(fo, _dp), _ptr(u, _dp))
     return fo, u
 
 
 def lb_steady(solid, force, tau=1.0, tol=1e-7, max_steps=200000, check_every=100, u_init=None):
-    """Steady BGK flow; returns (u[3,nz,ny,nx], steps, residual, converged)."""
+    """Steady BGK flow, force on the largest fluid cluster; returns (u[3,nz,ny,nx], steps,
+    residual, converged)."""
     s = np.ascontiguousarray(solid, dtype=np.uint8)
     nz, ny, nx = s.shape
     u = np.zeros((3,) + s.shape)

@@ -27,6 +27,10 @@
  *      Z(0) = sum_r pi(r) sum_i p_i(r) c_ig^2; D(t) = Z(0)/2 + sum_{m=1..t} Z(m).
  *  R6  Z and D are normalised by the total (free + adsorbed) tracer mass, which the
  *      Boltzmann weights of Sec. "Algorithm" make equal to one.
+ *  R15 The LB body force acts on the largest connected cluster of fluid nodes (D3Q19
+ *      links). In a sealed pocket a uniform force is balanced by pressure and the steady
+ *      velocity is zero; applying it there would only excite the undamped period-2
+ *      bounce-back mode of tiny pockets. Ties go to the cluster with the smallest node index.
  *  Parity of the porous-medium runs is pinned only by invariants (mass, Gamma/rho,
  *  Z(0) closed form): the paper prints no porous-medium numbers.
  */
@@ -106,6 +110,50 @@ int or_classify(int nx, int ny, int nz, const uint8_t* solid, uint8_t* cls,
     }
     if (n_fluid) *n_fluid = nf;
     if (n_iface) *n_iface = ni;
+    return 0;
+}
+
+/* Largest connected cluster of fluid nodes, two fluid nodes being connected when a D3Q19
+ * link joins them (periodic). in_cluster[n] = 1 on it, else 0; ties between equally large
+ * clusters go to the one holding the smallest node index. Plain breadth-first search. */
+int or_largest_cluster(int nx, int ny, int nz, const uint8_t* solid, uint8_t* in_cluster,
+                       int64_t* size_out)
+{
+    or_dims d = {nx, ny, nz};
+    int64_t N = (int64_t)nx * ny * nz;
+    int64_t* comp = malloc(sizeof(int64_t) * N);
+    int64_t* queue = malloc(sizeof(int64_t) * N);
+    if (!comp || !queue) {
+        free(comp);
+        free(queue);
+        return -1;
+    }
+    for (int64_t n = 0; n < N; ++n) comp[n] = -1;
+    int64_t best_root = -1, best_size = 0;
+    for (int64_t root = 0; root < N; ++root) {
+        if (solid[root] || comp[root] >= 0) continue;
+        int64_t head = 0, tail = 0;
+        queue[tail++] = root;
+        comp[root] = root;
+        while (head < tail) {
+            int64_t n = queue[head++];
+            for (int i = 1; i < NQ; ++i) {
+                int64_t m = neighbour(&d, n, i, +1);
+                if (!solid[m] && comp[m] < 0) {
+                    comp[m] = root;
+                    queue[tail++] = m;
+                }
+            }
+        }
+        if (tail > best_size) {
+            best_size = tail;
+            best_root = root;
+        }
+    }
+    for (int64_t n = 0; n < N; ++n) in_cluster[n] = (best_root >= 0 && comp[n] == best_root) ? 1 : 0;
+    if (size_out) *size_out = best_size;
+    free(comp);
+    free(queue);
     return 0;
 }
 
@@ -510,9 +558,10 @@ int or_lb_init(int nx, int ny, int nz, const uint8_t* solid, const double* u0, d
 /* One LB step: stream (pull; halfway bounce-back where r - c_i is solid), then
  * rho = sum f, u = (sum f c + F/2)/rho, then BGK collision with the Guo source
  *   f' = f - (f - f^eq(rho,u))/tau + (1 - 1/(2 tau)) w_i [3 (c_i - u) + 9 (c_i.u) c_i].F
- * Writes the post-collision f_out and the velocity u_out (3*N, zero on solid nodes). */
-int or_lb_step(int nx, int ny, int nz, const uint8_t* solid, const double F[3], double tau,
-               const double* f, double* f_out, double* u_out)
+ * Writes the post-collision f_out and the velocity u_out (3*N, zero on solid nodes).
+ * The force acts where forced[n] is nonzero (everywhere on the fluid when forced is NULL). */
+int or_lb_step(int nx, int ny, int nz, const uint8_t* solid, const uint8_t* forced,
+               const double F[3], double tau, const double* f, double* f_out, double* u_out)
 {
     or_dims d = {nx, ny, nz};
     int64_t N = (int64_t)nx * ny * nz;
@@ -538,7 +587,13 @@ int or_lb_step(int nx, int ny, int nz, const uint8_t* solid, const double F[3], 
             my += fi[i] * CY[i];
             mz += fi[i] * CZ[i];
         }
-        double u[3] = {(mx + 0.5 * F[0]) / rho, (my + 0.5 * F[1]) / rho, (mz + 0.5 * F[2]) / rho};
+        double Fn[3] = {0.0, 0.0, 0.0};
+        if (!forced || forced[n]) {
+            Fn[0] = F[0];
+            Fn[1] = F[1];
+            Fn[2] = F[2];
+        }
+        double u[3] = {(mx + 0.5 * Fn[0]) / rho, (my + 0.5 * Fn[1]) / rho, (mz + 0.5 * Fn[2]) / rho};
         double feq[NQ];
         lb_equilibrium(rho, u, feq);
         for (int i = 0; i < NQ; ++i) {
@@ -546,7 +601,7 @@ int or_lb_step(int nx, int ny, int nz, const uint8_t* solid, const double F[3], 
             double sx = 3.0 * (CX[i] - u[0]) + 9.0 * cu * CX[i];
             double sy = 3.0 * (CY[i] - u[1]) + 9.0 * cu * CY[i];
             double sz = 3.0 * (CZ[i] - u[2]) + 9.0 * cu * CZ[i];
-            double Si = (1.0 - 0.5 / tau) * WT[i] * (sx * F[0] + sy * F[1] + sz * F[2]);
+            double Si = (1.0 - 0.5 / tau) * WT[i] * (sx * Fn[0] + sy * Fn[1] + sz * Fn[2]);
             f_out[(int64_t)i * N + n] = fi[i] - (fi[i] - feq[i]) / tau + Si;
         }
         u_out[n] = u[0];
@@ -556,7 +611,8 @@ int or_lb_step(int nx, int ny, int nz, const uint8_t* solid, const double F[3], 
     return 0;
 }
 
-/* Runs LB steps from f^eq(1, u_init) until the residual
+/* Runs LB steps from f^eq(1, u_init), with the force on the largest fluid cluster (R15),
+ * until the residual
  *   res(t) = max over fluid nodes and components |u(t) - u(t-1)|
  * evaluated at every t that is a multiple of check_every (and at t = max_steps) is below
  * tol. u(0) = u_init (zero when NULL). Returns 0 when converged, 1 when max_steps ran out,
@@ -571,8 +627,10 @@ int or_lb_steady(int nx, int ny, int nz, const uint8_t* solid, const double F[3]
     double* fn = malloc(sizeof(double) * NQ * N);
     double* u = malloc(sizeof(double) * 3 * N);
     double* uprev = malloc(sizeof(double) * 3 * N);
-    if (!f || !fn || !u || !uprev) {
-        free(f); free(fn); free(u); free(uprev);
+    uint8_t* forced = malloc(N);
+    if (!f || !fn || !u || !uprev || !forced ||
+        or_largest_cluster(nx, ny, nz, solid, forced, NULL) != 0) {
+        free(f); free(fn); free(u); free(uprev); free(forced);
         return -1;
     }
     or_lb_init(nx, ny, nz, solid, u_init, f);
@@ -583,7 +641,7 @@ int or_lb_steady(int nx, int ny, int nz, const uint8_t* solid, const double F[3]
     int64_t t = 0;
     double res = INFINITY;
     while (t < max_steps) {
-        or_lb_step(nx, ny, nz, solid, F, tau, f, fn, u);
+        or_lb_step(nx, ny, nz, solid, forced, F, tau, f, fn, u);
         double* tmp = f; f = fn; fn = tmp;
         t += 1;
         if (t % check_every == 0 || t == max_steps) {
@@ -605,6 +663,6 @@ int or_lb_steady(int nx, int ny, int nz, const uint8_t* solid, const double F[3]
     memcpy(u_out, u, sizeof(double) * 3 * N);
     if (steps_out) *steps_out = t;
     if (residual_out) *residual_out = res;
-    free(f); free(fn); free(u); free(uprev);
+    free(f); free(fn); free(u); free(uprev); free(forced);
     return rc;
 }

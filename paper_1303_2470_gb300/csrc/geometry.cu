@@ -98,6 +98,78 @@ __global__ void k_list(const uint32_t* __restrict__ iface_w, const int32_t* __re
     if ((bits >> b) & 1u) ilist[ibase[n >> 5] + __popc(bits & ((1u << b) - 1u))] = n;
 }
 
+// Connected components by monotone min-label propagation: every fluid node starts with its
+// own index and repeatedly takes the smallest label among itself, its label's label
+// (pointer jumping) and its fluid D3Q19 neighbours. Labels only decrease and always name a
+// node of the same cluster, so races between threads only delay convergence; the fixed
+// point is the smallest node index of each cluster, whatever the schedule.
+__global__ void k_cc_init(const uint32_t* __restrict__ fluid_w, int N, int* __restrict__ label)
+{
+    int n = blockIdx.x * blockDim.x + threadIdx.x;
+    if (n < N) label[n] = ((fluid_w[n >> 5] >> (n & 31)) & 1u) ? n : 0x7fffffff;
+}
+
+__global__ void k_cc_sweep(const uint32_t* __restrict__ fluid_w, int nx, int ny, int nz, int N, int* label,
+                           int* __restrict__ changed)
+{
+    int n = blockIdx.x * blockDim.x + threadIdx.x;
+    if (n >= N || !((fluid_w[n >> 5] >> (n & 31)) & 1u)) return;
+    volatile int* lab = label;
+    int cur = lab[n];
+    int l = cur;
+    int l2 = lab[l];
+    if (l2 < l) l = l2;
+    int x = n % nx, y = (n / nx) % ny, z = n / (nx * ny);
+#pragma unroll
+    for (int i = 1; i < kQ; ++i) {
+        int xs = x + cx(i), ys = y + cy(i), zs = z + cz(i);
+        xs = xs < 0 ? xs + nx : (xs >= nx ? xs - nx : xs);
+        ys = ys < 0 ? ys + ny : (ys >= ny ? ys - ny : ys);
+        zs = zs < 0 ? zs + nz : (zs >= nz ? zs - nz : zs);
+        int m = xs + nx * (ys + ny * zs);
+        if ((fluid_w[m >> 5] >> (m & 31)) & 1u) {
+            int lm = lab[m];
+            if (lm < l) l = lm;
+        }
+    }
+    if (l < cur) {
+        atomicMin(label + n, l);
+        *changed = 1;
+    }
+}
+
+__global__ void k_cc_count(const uint32_t* __restrict__ fluid_w, int N, const int* __restrict__ label,
+                           int* __restrict__ count)
+{
+    int n = blockIdx.x * blockDim.x + threadIdx.x;
+    if (n < N && ((fluid_w[n >> 5] >> (n & 31)) & 1u)) atomicAdd(count + label[n], 1);
+}
+
+// key = size << 32 | (0xffffffff - root): the maximum is the largest cluster, ties to the
+// smallest root index
+__global__ void k_cc_best(const int* __restrict__ count, int N, unsigned long long* __restrict__ best)
+{
+    int n = blockIdx.x * blockDim.x + threadIdx.x;
+    unsigned long long key = 0ull;
+    if (n < N && count[n] > 0) key = ((unsigned long long)count[n] << 32) | (0xffffffffull - (unsigned)n);
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        unsigned long long v = __shfl_xor_sync(0xffffffffu, key, o);
+        key = v > key ? v : key;
+    }
+    if ((threadIdx.x & 31) == 0 && key) atomicMax(best, key);
+}
+
+__global__ void k_cc_mark(const uint32_t* __restrict__ fluid_w, int N, int W, const int* __restrict__ label,
+                          const unsigned long long* __restrict__ best, uint32_t* __restrict__ cluster_w)
+{
+    int n = blockIdx.x * blockDim.x + threadIdx.x;
+    const int root = (int)(0xffffffffull - (*best & 0xffffffffull));
+    bool in = n < N && ((fluid_w[n >> 5] >> (n & 31)) & 1u) && label[n] == root;
+    unsigned b = __ballot_sync(0xffffffffu, in);
+    if ((threadIdx.x & 31) == 0 && (n >> 5) < W) cluster_w[n >> 5] = b;
+}
+
 template <typename T>
 int dev_alloc(T** p, size_t count, cudaStream_t s, bool stream_ordered)
 {
@@ -139,10 +211,67 @@ int cuda_fail(cudaError_t e, const char* what)
 
 void free_geometry(Geometry* g, cudaStream_t s, bool so)
 {
+    dev_free(g->cluster, s, so);
     dev_free(g->fluid, s, so);
     dev_free(g->iface, s, so);
     dev_free(g->ibase, s, so);
     dev_free(g->ilist, s, so);
+}
+
+int build_cluster(Geometry* G, cudaStream_t s, bool so)
+{
+    int* label = nullptr;
+    int* count = nullptr;
+    int* changed = nullptr;
+    unsigned long long* best = nullptr;
+    int rc;
+    if ((rc = dev_alloc(&G->cluster, G->W, s, so)) || (rc = dev_alloc(&label, G->N, s, so)) ||
+        (rc = dev_alloc(&count, G->N, s, so)) || (rc = dev_alloc(&changed, 1, s, so)) ||
+        (rc = dev_alloc(&best, 1, s, so))) {
+        dev_free(label, s, so);
+        dev_free(count, s, so);
+        dev_free(changed, s, so);
+        dev_free(best, s, so);
+        return rc;
+    }
+    const int threads = 256, blocks = (G->N + threads - 1) / threads;
+    const int wblocks = (int)(((long long)G->W * 32 + threads - 1) / threads);
+    cudaError_t e = cudaSuccess;
+    k_cc_init<<<blocks, threads, 0, s>>>(G->fluid, G->N, label);
+    // sweep until a whole pass changes nothing; the flag is read every 8 passes
+    for (int pass = 0; e == cudaSuccess; pass += 8) {
+        int h_changed = 0;
+        e = cudaMemsetAsync(changed, 0, sizeof(int), s);
+        for (int k = 0; k < 8 && e == cudaSuccess; ++k) {
+            k_cc_sweep<<<blocks, threads, 0, s>>>(G->fluid, G->nx, G->ny, G->nz, G->N, label, changed);
+            e = cudaGetLastError();
+        }
+        if (e == cudaSuccess) e = cudaMemcpyAsync(&h_changed, changed, sizeof(int), cudaMemcpyDeviceToHost, s);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+        if (e != cudaSuccess || !h_changed) break;
+        if (pass > 4 * (G->nx + G->ny + G->nz) + G->N) {  // cannot happen: labels strictly decrease
+            e = cudaErrorUnknown;
+            break;
+        }
+    }
+    if (e == cudaSuccess) e = cudaMemsetAsync(count, 0, sizeof(int) * (size_t)G->N, s);
+    if (e == cudaSuccess) e = cudaMemsetAsync(best, 0, sizeof(unsigned long long), s);
+    if (e == cudaSuccess) {
+        k_cc_count<<<blocks, threads, 0, s>>>(G->fluid, G->N, label, count);
+        k_cc_best<<<blocks, threads, 0, s>>>(count, G->N, best);
+        k_cc_mark<<<wblocks, threads, 0, s>>>(G->fluid, G->N, G->W, label, best, G->cluster);
+        e = cudaGetLastError();
+    }
+    unsigned long long h_best = 0;
+    if (e == cudaSuccess) e = cudaMemcpyAsync(&h_best, best, sizeof(h_best), cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    dev_free(label, s, so);
+    dev_free(count, s, so);
+    dev_free(changed, s, so);
+    dev_free(best, s, so);
+    if (e != cudaSuccess) return cuda_fail(e, "connected clusters");
+    G->n_cluster = (int64_t)(h_best >> 32);
+    return MP_OK;
 }
 
 int build_geometry(const mp_geometry* g, cudaStream_t s, bool so, bool want_list, Geometry* out)
@@ -228,3 +357,51 @@ int build_geometry(const mp_geometry* g, cudaStream_t s, bool so, bool want_list
 }
 
 }  // namespace mp
+
+extern "C" int mp_classify(const mp_geometry* g, uint8_t* cls, int64_t* n_fluid, int64_t* n_interface,
+                           int64_t* n_cluster, void* stream)
+{
+    using namespace mp;
+    clear_error();
+    if (!cls) {
+        set_error("mp_classify: cls is NULL");
+        return MP_EINVAL;
+    }
+    cudaStream_t s = (cudaStream_t)stream;
+    Geometry G;
+    int rc = build_geometry(g, s, true, false, &G);
+    if (rc == MP_OK) rc = build_cluster(&G, s, true);
+    if (rc != MP_OK) {
+        free_geometry(&G, s, true);
+        cudaStreamSynchronize(s);
+        return rc;
+    }
+    const size_t W = (size_t)G.W;
+    uint32_t* h = (uint32_t*)malloc(3 * W * sizeof(uint32_t));
+    if (!h) {
+        free_geometry(&G, s, true);
+        cudaStreamSynchronize(s);
+        set_error("host allocation failed");
+        return MP_ENOMEM;
+    }
+    cudaError_t e = cudaMemcpyAsync(h, G.fluid, W * 4, cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(h + W, G.iface, W * 4, cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(h + 2 * W, G.cluster, W * 4, cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    if (e == cudaSuccess) {
+        for (int n = 0; n < G.N; ++n) {
+            const uint32_t b = 1u << (n & 31);
+            const size_t w = (size_t)(n >> 5);
+            cls[n] = (uint8_t)((h[w] & b ? 1 : 0) + (h[W + w] & b ? 1 : 0) + (h[2 * W + w] & b ? 4 : 0));
+        }
+        if (n_fluid) *n_fluid = G.n_fluid;
+        if (n_interface) *n_interface = G.n_iface;
+        if (n_cluster) *n_cluster = G.n_cluster;
+    }
+    free(h);
+    free_geometry(&G, s, true);
+    cudaStreamSynchronize(s);
+    if (e != cudaSuccess) return cuda_fail(e, "mp_classify");
+    return MP_OK;
+}
+

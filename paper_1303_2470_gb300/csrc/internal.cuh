@@ -65,6 +65,8 @@ struct Geometry {
     uint32_t* iface = nullptr;
     int32_t* ibase = nullptr;
     int32_t* ilist = nullptr;
+    uint32_t* cluster = nullptr;  // bit set = node of the largest connected fluid cluster
+    int64_t n_cluster = 0;
 };
 
 // Error reporting: the thread-local last-error text behind mp_last_error().
@@ -84,5 +86,9 @@ int cuda_fail(cudaError_t e, const char* what);
 int build_geometry(const mp_geometry* g, cudaStream_t stream, bool stream_ordered,
                    bool want_list, Geometry* out);
 void free_geometry(Geometry* g, cudaStream_t stream, bool stream_ordered);
+
+// Largest connected cluster of fluid nodes (D3Q19 links, periodic) into g->cluster and
+// g->n_cluster; ties go to the cluster holding the smallest node index. Synchronises.
+int build_cluster(Geometry* g, cudaStream_t stream, bool stream_ordered);
 
 }  // namespace mp

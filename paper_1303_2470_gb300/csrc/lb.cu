@@ -8,6 +8,8 @@
 // Populations are FP32 deviations g_i = f_i - w_i, structure of arrays g[i*N + n], which
 // keeps ~9 significant digits of the O(u) part that sets the velocity. Only fluid nodes
 // are read or written. The steady criterion max|u(t) - u(t-1)| is evaluated in FP64.
+// The body force acts on the largest connected fluid cluster only (sealed pockets stay at
+// rest, their steady Stokes velocity).
 #include <cmath>
 #include <cstring>
 #include <string>
@@ -23,6 +25,7 @@ constexpr int kLbThreads = 256;
 struct LbArgs {
     int nx, ny, nz, N;
     const uint32_t* fluid;
+    const uint32_t* forced;  // the force acts on these nodes (the largest fluid cluster)
     float Fx, Fy, Fz;
     float inv_tau;
     float guo;  // 1 - 1/(2 tau)
@@ -67,18 +70,20 @@ __global__ void __launch_bounds__(kLbThreads)
                 my += float(cy(i)) * f[i];
                 mz += float(cz(i)) * f[i];
             }
+            const bool on = lb_bit(a.forced, n);
+            const float Fx = on ? a.Fx : 0.0f, Fy = on ? a.Fy : 0.0f, Fz = on ? a.Fz : 0.0f;
             const float rho = 1.0f + drho;
             const float inv_rho = 1.0f / rho;
-            const float ux = (mx + 0.5f * a.Fx) * inv_rho;
-            const float uy = (my + 0.5f * a.Fy) * inv_rho;
-            const float uz = (mz + 0.5f * a.Fz) * inv_rho;
+            const float ux = (mx + 0.5f * Fx) * inv_rho;
+            const float uy = (my + 0.5f * Fy) * inv_rho;
+            const float uz = (mz + 0.5f * Fz) * inv_rho;
             const float uu = ux * ux + uy * uy + uz * uz;
-            const float uF = ux * a.Fx + uy * a.Fy + uz * a.Fz;
+            const float uF = ux * Fx + uy * Fy + uz * Fz;
 #pragma unroll
             for (int i = 0; i < kQ; ++i) {
                 const float w = weight<float>(i);
                 const float cu = float(cx(i)) * ux + float(cy(i)) * uy + float(cz(i)) * uz;
-                const float cF = float(cx(i)) * a.Fx + float(cy(i)) * a.Fy + float(cz(i)) * a.Fz;
+                const float cF = float(cx(i)) * Fx + float(cy(i)) * Fy + float(cz(i)) * Fz;
                 // f^eq - w = w [(rho - 1) + rho (3 cu + 4.5 cu^2 - 1.5 uu)]
                 const float geq = w * (drho + rho * (3.0f * cu + 4.5f * cu * cu - 1.5f * uu));
                 const float src = a.guo * w * (3.0f * (cF - uF) + 9.0f * cu * cF);
@@ -146,6 +151,14 @@ extern "C" int lb_steady(const mp_geometry* geom, const double force[3], double 
     Geometry G;
     int rc = build_geometry(geom, s, true, false, &G);
     if (rc != MP_OK) return rc;
+    // the body force acts on the largest connected fluid cluster: in a sealed pocket a
+    // uniform force is balanced by pressure and the steady velocity is zero
+    rc = build_cluster(&G, s, true);
+    if (rc != MP_OK) {
+        free_geometry(&G, s, true);
+        cudaStreamSynchronize(s);
+        return rc;
+    }
     const size_t N = (size_t)G.N;
     float *g0 = nullptr, *g1 = nullptr, *uprev = nullptr;
     unsigned long long* res_d = nullptr;
@@ -172,6 +185,7 @@ extern "C" int lb_steady(const mp_geometry* geom, const double force[3], double 
     a.nz = G.nz;
     a.N = G.N;
     a.fluid = G.fluid;
+    a.forced = G.cluster;
     a.Fx = (float)force[0];
     a.Fy = (float)force[1];
     a.Fz = (float)force[2];

@@ -71,8 +71,10 @@ _lib.mp_free.argtypes = [_c_vp]
 _lib.mp_free.restype = None
 _lib.lb_steady.argtypes = [ctypes.POINTER(mp_geometry), _dp, _c_dbl, _c_dbl, _c_i64, _c_i64, _c_vp,
                            _c_vp, ctypes.POINTER(_c_i64), _dp, _c_vp]
+_lib.mp_classify.argtypes = [ctypes.POINTER(mp_geometry), _c_vp, ctypes.POINTER(_c_i64),
+                             ctypes.POINTER(_c_i64), ctypes.POINTER(_c_i64), _c_vp]
 for _f in ("mp_init", "mp_init_batch", "mp_step", "mp_vacf", "mp_mass", "mp_info", "mp_get_field",
-           "mp_set_field", "lb_steady"):
+           "mp_set_field", "lb_steady", "mp_classify"):
     getattr(_lib, _f).restype = _c_int
 
 
@@ -233,6 +235,18 @@ def mp_set_field(ctx: Context, species: int, field: int, free, ads=None):
     ad = None if ads is None else np.ascontiguousarray(ads, dtype=np.float64)
     _check(_lib.mp_set_field(ctx.ptr, species, field, fr.ctypes.data_as(_dp),
                              ad.ctypes.data_as(_dp) if ad is not None else None))
+
+
+def mp_classify(solid, stream=None):
+    """Node classes (0 solid, 1 fluid, 2 interfacial, +4 in the largest fluid cluster) as a
+    uint8 array shaped like `solid`, and the counts (n_fluid, n_interface, n_cluster)."""
+    g, keep = make_geometry(solid)
+    cls = np.zeros((g.nz, g.ny, g.nx), dtype=np.uint8)
+    nf, ni, nc = _c_i64(), _c_i64(), _c_i64()
+    _check(_lib.mp_classify(ctypes.byref(g), cls.ctypes.data, ctypes.byref(nf), ctypes.byref(ni),
+                            ctypes.byref(nc), _stream(stream)))
+    del keep
+    return cls, (nf.value, ni.value, nc.value)
 
 
 def mp_free(ctx: Context):

@@ -28,9 +28,12 @@ def _u_dev(shape):
 
 
 def test_fixed_steps_porous_medium(mp):
-    """Ragged 23x26x19 random medium, body force in two directions, tau = 0.8: u after 400
-    steps agrees with the oracle's."""
-    solid, _ = media.random_spheres((19, 26, 23), 3, 0.55, seed=5)
+    """Ragged 23x26x19 random medium with a sealed pocket, body force in three directions,
+    tau = 0.8: u after 400 steps agrees with the oracle's; the pocket stays at rest."""
+    solid, _ = media.random_spheres((19, 26, 23), 3, 0.35, seed=5)
+    inc, size = oracle.largest_cluster(solid)
+    pocket = (solid == 0) & (inc == 0)
+    assert pocket.sum() >= 1
     F = (2e-5, -1e-5, 0.5e-5)
     u = _u_dev(solid.shape)
     steps, res, conv = mp.lb_steady(solid, F, u, tau=0.8, tol=0.0, max_steps=400, check_every=50)
@@ -41,6 +44,33 @@ def test_fixed_steps_porous_medium(mp):
     assert np.max(np.abs(ug - uo)) < 1e-4 * scale
     assert abs(res - ro) < 1e-3 * ro + 1e-12
     assert np.all(ug[:, solid.astype(bool)] == 0.0)
+    assert np.all(ug[:, pocket] == 0.0)
+
+
+def test_classify_matches_oracle(mp):
+    """Node classes and the largest fluid cluster are integer work: bit-exact."""
+    for shape, R, phi, seed in [((13, 17, 21), 3, 0.5, 1), ((24, 24, 24), 3, 0.30, 7),
+                                ((128, 128, 128), 6, 0.40, 1)]:
+        solid, _ = media.random_spheres(shape, R, phi, seed)
+        for arg in (solid, torch.as_tensor(solid).cuda()):
+            cls, (nf, ni, nc) = mp.mp_classify(arg)
+            ocls, onf, oni = oracle.classify(solid)
+            inc, size = oracle.largest_cluster(solid)
+            assert np.array_equal(cls & 3, ocls)
+            assert np.array_equal((cls >> 2) & 1, inc)
+            assert (nf, ni, nc) == (onf, oni, size)
+
+
+def test_porous_flow_reaches_the_steady_criterion(mp):
+    """128^3 random spheres (R = 6, porosity 0.40, seed 1) at a force giving mean u ~ 0.01:
+    with the force on the percolating cluster the residual falls below 1e-7."""
+    solid, _ = media.random_spheres((128, 128, 128), 6, 0.40, 1)
+    sd = torch.as_tensor(solid).cuda()
+    u = _u_dev(solid.shape)
+    steps, res, conv = mp.lb_steady(sd, (1.83e-3, 0, 0), u, tol=1e-7, max_steps=100_000, check_every=100)
+    assert conv and res < 1e-7
+    fl = sd == 0
+    assert 0.008 < float(u[0][fl].mean()) < 0.012
 
 
 def test_rest_stays_at_rest(mp):

@@ -60,3 +60,55 @@ def test_steady_criterion_and_step_budget():
     assert abs(u[0].max() - 0.05) < 2e-3
     u2, steps2, res2, conv2 = oracle.lb_steady(solid, (F, 0, 0), 1.0, 1e-7, steps - 100, 100)
     assert not conv2 and steps2 == steps - 100 and res2 >= 1e-7
+
+
+def _periodic_d3q19_components(solid):
+    """Connected components of the fluid nodes under the 18 D3Q19 links (periodic), by
+    scipy's graph routine: an implementation independent of the oracle's search."""
+    from scipy.sparse import coo_matrix
+    from scipy.sparse.csgraph import connected_components
+    nz, ny, nx = solid.shape
+    idx = np.arange(solid.size).reshape(solid.shape)
+    fluid = solid == 0
+    rows, cols = [], []
+    for c in [(a, b, d) for a in (-1, 0, 1) for b in (-1, 0, 1) for d in (-1, 0, 1)
+              if 1 <= abs(a) + abs(b) + abs(d) <= 2]:
+        nb = np.roll(idx, shift=(-c[2], -c[1], -c[0]), axis=(0, 1, 2))
+        ok = fluid & fluid.reshape(-1)[nb]
+        rows.append(idx[ok])
+        cols.append(nb[ok])
+    r, c = np.concatenate(rows), np.concatenate(cols)
+    g = coo_matrix((np.ones(r.size), (r, c)), shape=(solid.size, solid.size))
+    _, lab = connected_components(g, directed=False)
+    return lab.reshape(solid.shape)
+
+
+def test_largest_cluster_matches_graph_components():
+    for seed, (shape, R, phi) in enumerate([((12, 14, 10), 2, 0.45), ((20, 20, 20), 3, 0.35),
+                                            ((9, 11, 13), 1.5, 0.5)]):
+        solid, _ = media.random_spheres(shape, R, phi, seed=seed + 21)
+        inc, size = oracle.largest_cluster(solid)
+        lab = _periodic_d3q19_components(solid)
+        fl = solid == 0
+        sizes = np.bincount(lab[fl])
+        assert size == sizes.max()
+        best = [l for l in np.unique(lab[fl]) if sizes[l] == sizes.max()]
+        # ties go to the cluster holding the smallest node index
+        first = min(best, key=lambda l: np.flatnonzero((lab == l).reshape(-1) & fl.reshape(-1))[0])
+        assert np.array_equal(inc.astype(bool), fl & (lab == first))
+
+
+def test_sealed_pockets_stay_at_rest_and_the_flow_converges():
+    """A channel plus a sealed single-node pocket and a sealed two-node pocket: the force acts
+    on the channel only, the pockets keep u = 0 exactly, and the residual falls below tol
+    (with the force on a one-node pocket its velocity would flip sign every step)."""
+    solid = np.ones((9, 9, 12), dtype=np.uint8)
+    solid[2:6, 2:6, :] = 0                 # channel along x, periodic
+    solid[7, 7, 3] = 0                     # sealed single node
+    solid[7, 1, 5:7] = 0                   # sealed pair along x
+    inc, size = oracle.largest_cluster(solid)
+    assert size == 16 * 12 and inc[7, 7, 3] == 0 and inc[7, 1, 5] == 0
+    u, steps, res, conv = oracle.lb_steady(solid, (1e-5, 0, 0), tol=1e-12, max_steps=20000, check_every=50)
+    assert conv and res < 1e-12
+    assert np.all(u[:, 7, 7, 3] == 0.0) and np.all(u[:, 7, 1, 5:7] == 0.0)
+    assert u[0, 4, 4, 0] > 0
