@@ -55,7 +55,7 @@ WORKLOAD = {
 }
 # LB steps to steady state of this workload, measured by the GPU arm (cold start); used only
 # to scale the oracle's per-step CPU times to a whole job in the reference arm.
-LB_STEPS_ASSUMED = 4000
+LB_STEPS_ASSUMED = 2000
 
 METRIC = "sorption-MP node-species updates/s (whole job incl. LB to steady)"
 UNIT = "node-species updates/s"

@@ -205,7 +205,10 @@ const char* mp_last_error(void);
  *  tol           stop at the first checked step t with max |u(t) - u(t-1)| < tol, taken
  *                over fluid nodes and components.
  *  max_steps     step budget (>= 1); check_every: residual period (>= 1); the residual is
- *                also taken at t = max_steps.
+ *                also taken at t = max_steps. After every check that fails (before
+ *                max_steps) the populations are replaced by the mean of the last two
+ *                iterates: this keeps the fixed point and removes the undamped period-2
+ *                modes that bounce-back sustains at nodes with few open links.
  *  u_init        device, FP32 3*N, or NULL: start from f^eq(rho = 1, u_init) (cold start
  *                from rest when NULL).
  *  u_out         device, FP32 3*N: u at the final step, zero on solid nodes.

@@ -31,6 +31,11 @@
  *      links). In a sealed pocket a uniform force is balanced by pressure and the steady
  *      velocity is zero; applying it there would only excite the undamped period-2
  *      bounce-back mode of tiny pockets. Ties go to the cluster with the smallest node index.
+ *  R16 Steady LB flow: at every residual check that fails, the populations are replaced
+ *      by the mean of the last two iterates before stepping on. This leaves the fixed
+ *      point of the update unchanged and removes the undamped period-2 modes that
+ *      bounce-back sustains at nodes with few open links (for a lone node under a force
+ *      the momentum alternates m, -(m + F) forever; the mean is the fixed point u = 0).
  *  Parity of the porous-medium runs is pinned only by invariants (mass, Gamma/rho,
  *  Z(0) closed form): the paper prints no porous-medium numbers.
  */
@@ -611,8 +616,8 @@ int or_lb_step(int nx, int ny, int nz, const uint8_t* solid, const uint8_t* forc
     return 0;
 }
 
-/* Runs LB steps from f^eq(1, u_init), with the force on the largest fluid cluster (R15),
- * until the residual
+/* Runs LB steps from f^eq(1, u_init), with the force on the largest fluid cluster (R15)
+ * and the two-iterate mean at failed checks (R16), until the residual
  *   res(t) = max over fluid nodes and components |u(t) - u(t-1)|
  * evaluated at every t that is a multiple of check_every (and at t = max_steps) is below
  * tol. u(0) = u_init (zero when NULL). Returns 0 when converged, 1 when max_steps ran out,
@@ -657,6 +662,12 @@ int or_lb_steady(int nx, int ny, int nz, const uint8_t* solid, const double F[3]
                 rc = 0;
                 break;
             }
+            /* R16: replace the state by the mean of the last two iterates (f holds t, fn
+             * holds t-1). The fixed point is unchanged; an error mode with eigenvalue lambda
+             * is scaled by (1 + lambda)/2, which removes the undamped period-2 modes that
+             * bounce-back sustains at strongly confined nodes. */
+            if (t < max_steps)
+                for (int64_t k = 0; k < (int64_t)NQ * N; ++k) f[k] = 0.5 * (f[k] + fn[k]);
         }
         memcpy(uprev, u, sizeof(double) * 3 * N);
     }

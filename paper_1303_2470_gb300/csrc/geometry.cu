@@ -44,11 +44,12 @@ __global__ void k_classify(const uint8_t* __restrict__ solid, int nx, int ny, in
     }
 }
 
-// single block: exclusive prefix of popc(iface_w) into ibase, and the two totals
+// single block: exclusive prefixes of popc(iface_w) into ibase and of popc(fluid_w) into
+// fbase, and the two totals
 constexpr int kScanThreads = 1024;
 __global__ void __launch_bounds__(kScanThreads)
     k_scan(const uint32_t* __restrict__ fluid_w, const uint32_t* __restrict__ iface_w, int W,
-           int32_t* __restrict__ ibase, long long* __restrict__ totals)
+           int32_t* __restrict__ ibase, int32_t* __restrict__ fbase, long long* __restrict__ totals)
 {
     __shared__ long long s_i[kScanThreads / 32], s_f[kScanThreads / 32];
     int per = (W + kScanThreads - 1) / kScanThreads;
@@ -82,20 +83,37 @@ __global__ void __launch_bounds__(kScanThreads)
         ibase[w] = (int32_t)excl;
         excl += __popc(iface_w[w]);
     }
+    // the same for the fluid bits (second pass over this thread's words)
+    __syncthreads();
+    long long incf = cf;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        long long v = __shfl_up_sync(0xffffffffu, incf, o);
+        if (lane >= o) incf += v;
+    }
+    if (lane == 31) s_i[warp] = incf;
+    __syncthreads();
+    long long beforef = 0;
+    for (int k = 0; k < warp; ++k) beforef += s_i[k];
+    long long exclf = beforef + incf - cf;
+    for (int w = lo; w < hi; ++w) {
+        fbase[w] = (int32_t)exclf;
+        exclf += __popc(fluid_w[w]);
+    }
     if (threadIdx.x == 0) {
         totals[0] = tot_f;
         totals[1] = tot_i;
     }
 }
 
-__global__ void k_list(const uint32_t* __restrict__ iface_w, const int32_t* __restrict__ ibase, int N,
-                       int32_t* __restrict__ ilist)
+__global__ void k_list(const uint32_t* __restrict__ bits_w, const int32_t* __restrict__ base, int N,
+                       int32_t* __restrict__ list)
 {
     int n = blockIdx.x * blockDim.x + threadIdx.x;
     if (n >= N) return;
-    uint32_t bits = iface_w[n >> 5];
+    uint32_t bits = bits_w[n >> 5];
     int b = n & 31;
-    if ((bits >> b) & 1u) ilist[ibase[n >> 5] + __popc(bits & ((1u << b) - 1u))] = n;
+    if ((bits >> b) & 1u) list[base[n >> 5] + __popc(bits & ((1u << b) - 1u))] = n;
 }
 
 // Connected components by monotone min-label propagation: every fluid node starts with its
@@ -216,6 +234,8 @@ void free_geometry(Geometry* g, cudaStream_t s, bool so)
     dev_free(g->iface, s, so);
     dev_free(g->ibase, s, so);
     dev_free(g->ilist, s, so);
+    dev_free(g->fbase, s, so);
+    dev_free(g->flist, s, so);
 }
 
 int build_cluster(Geometry* G, cudaStream_t s, bool so)
@@ -303,7 +323,8 @@ int build_geometry(const mp_geometry* g, cudaStream_t s, bool so, bool want_list
     uint8_t* solid_d = nullptr;
     long long* totals = nullptr;
     if ((rc = dev_alloc(&G.fluid, G.W, s, so)) || (rc = dev_alloc(&G.iface, G.W, s, so)) ||
-        (rc = dev_alloc(&G.ibase, G.W, s, so)) || (rc = dev_alloc(&totals, 2, s, so))) {
+        (rc = dev_alloc(&G.ibase, G.W, s, so)) || (rc = dev_alloc(&G.fbase, G.W, s, so)) ||
+        (rc = dev_alloc(&totals, 2, s, so))) {
         free_geometry(&G, s, so);
         dev_free(totals, s, so);
         return rc;
@@ -327,7 +348,7 @@ int build_geometry(const mp_geometry* g, cudaStream_t s, bool so, bool want_list
     int threads = 256;
     int blocks = (int)(((long long)G.W * 32 + threads - 1) / threads);
     k_classify<<<blocks, threads, 0, s>>>(solid, G.nx, G.ny, G.nz, G.N, G.W, G.fluid, G.iface);
-    k_scan<<<1, kScanThreads, 0, s>>>(G.fluid, G.iface, G.W, G.ibase, totals);
+    k_scan<<<1, kScanThreads, 0, s>>>(G.fluid, G.iface, G.W, G.ibase, G.fbase, totals);
     long long h_tot[2] = {0, 0};
     cudaError_t e = cudaGetLastError();
     if (e == cudaSuccess) e = cudaMemcpyAsync(h_tot, totals, sizeof(h_tot), cudaMemcpyDeviceToHost, s);
@@ -340,16 +361,18 @@ int build_geometry(const mp_geometry* g, cudaStream_t s, bool so, bool want_list
     }
     G.n_fluid = h_tot[0];
     G.n_iface = h_tot[1];
-    if (want_list && G.n_iface > 0) {
-        if ((rc = dev_alloc(&G.ilist, (size_t)G.n_iface, s, so))) {
+    if (want_list) {
+        if ((G.n_iface > 0 && (rc = dev_alloc(&G.ilist, (size_t)G.n_iface, s, so))) ||
+            (G.n_fluid > 0 && (rc = dev_alloc(&G.flist, (size_t)G.n_fluid, s, so)))) {
             free_geometry(&G, s, so);
             return rc;
         }
-        k_list<<<(G.N + 255) / 256, 256, 0, s>>>(G.iface, G.ibase, G.N, G.ilist);
+        if (G.n_iface > 0) k_list<<<(G.N + 255) / 256, 256, 0, s>>>(G.iface, G.ibase, G.N, G.ilist);
+        if (G.n_fluid > 0) k_list<<<(G.N + 255) / 256, 256, 0, s>>>(G.fluid, G.fbase, G.N, G.flist);
         e = cudaGetLastError();
         if (e != cudaSuccess) {
             free_geometry(&G, s, so);
-            return cuda_fail(e, "interface list");
+            return cuda_fail(e, "node lists");
         }
     }
     *out = G;

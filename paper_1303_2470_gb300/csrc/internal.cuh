@@ -55,6 +55,7 @@ __host__ __device__ constexpr T weight(int i)
 //   ibase[w]  number of interfacial nodes before node 32w (exclusive prefix), so the
 //             compact index of interfacial node n is ibase[n>>5] + popc(iface[n>>5] & lt)
 //   ilist[k]  node index of the k-th interfacial node, increasing
+//   fbase[w], flist[k]  the same prefix and list for all fluid nodes (work list of the MP)
 // ---------------------------------------------------------------------------------------
 struct Geometry {
     int nx = 0, ny = 0, nz = 0;
@@ -65,6 +66,8 @@ struct Geometry {
     uint32_t* iface = nullptr;
     int32_t* ibase = nullptr;
     int32_t* ilist = nullptr;
+    int32_t* fbase = nullptr;
+    int32_t* flist = nullptr;
     uint32_t* cluster = nullptr;  // bit set = node of the largest connected fluid cluster
     int64_t n_cluster = 0;
 };
@@ -81,7 +84,7 @@ int cuda_fail(cudaError_t e, const char* what);
     } while (0)
 
 // Geometry prep (geometry.cu): validates the mask, classifies nodes and builds the packed
-// arrays above on `stream`. Allocates with cudaMallocAsync on the stream when
+// arrays above on `stream` (the two node lists only when `want_list`). Allocates with cudaMallocAsync on the stream when
 // `stream_ordered`, else with cudaMalloc. Synchronises the stream (counts go to the host).
 int build_geometry(const mp_geometry* g, cudaStream_t stream, bool stream_ordered,
                    bool want_list, Geometry* out);

@@ -9,7 +9,11 @@
 // keeps ~9 significant digits of the O(u) part that sets the velocity. Only fluid nodes
 // are read or written. The steady criterion max|u(t) - u(t-1)| is evaluated in FP64.
 // The body force acts on the largest connected fluid cluster only (sealed pockets stay at
-// rest, their steady Stokes velocity).
+// rest, their steady Stokes velocity). At every failed residual check the state is replaced
+// by the mean of the last two iterates: the fixed point is unchanged, an error mode of
+// eigenvalue lambda is scaled by (1 + lambda)/2, and the undamped period-2 modes that
+// bounce-back sustains at nodes with few open links disappear (without it the residual of a
+// porous medium stalls near |F|).
 #include <cmath>
 #include <cstring>
 #include <string>
@@ -111,6 +115,13 @@ __global__ void __launch_bounds__(kLbThreads)
         for (int o = 16; o > 0; o >>= 1) res = fmax(res, __shfl_xor_sync(0xffffffffu, res, o));
         if ((threadIdx.x & 31) == 0 && res > 0.0) atomicMax(res_bits, (unsigned long long)__double_as_longlong(res));
     }
+}
+
+// g0 <- (g0 + g1) / 2 over all populations: the mean of the last two iterates
+__global__ void k_lb_mean(float* __restrict__ g0, const float* __restrict__ g1, size_t count)
+{
+    for (size_t k = blockIdx.x * (size_t)blockDim.x + threadIdx.x; k < count; k += (size_t)gridDim.x * blockDim.x)
+        g0[k] = 0.5f * (g0[k] + g1[k]);
 }
 
 // f = f^eq(rho = 1, u0) (u0 = 0 when NULL) as deviations; u_prev = u0
@@ -219,6 +230,12 @@ extern "C" int lb_steady(const mp_geometry* geom, const double force[3], double 
             if (res < tol) {
                 converged = true;
                 break;
+            }
+            // the mean of the last two iterates (g0 = t, g1 = t-1): same fixed point, and the
+            // undamped period-2 modes that bounce-back sustains at confined nodes vanish
+            if (t < max_steps) {
+                k_lb_mean<<<2 * 152 * 4, 256, 0, s>>>(g0, g1, (size_t)kQ * N);
+                e = cudaGetLastError();
             }
         }
     }

@@ -7,10 +7,17 @@
 //   Xa(r,t+1)  = p_a X(r) + (1 - p_d) Xa(r)            on interfacial nodes
 //   X(r,t+1)   = P*(r) + p_d Xa(r)                      on interfacial nodes
 // with p_i(s) = w_i [lambda/2 + 3 c_i.u(s) + 9/2 (c_i.u(s))^2 - 3/2 u(s).u(s)] on links
-// whose far end is fluid, zero otherwise; lambda = 12 D_b; p_a = k_a, p_d = k_d. Every
-// species sharing the medium uses the same advective part of p_i, which is computed once
-// per link and node; only lambda/2, p_a and p_d differ per species.
+// whose far end is fluid, zero otherwise; lambda = 12 D_b; p_a = k_a, p_d = k_d.
+// The step is evaluated as X + sum of net link fluxes (see k_step), which is the same
+// update in exact arithmetic and conserves mass in FP32.
 // The VACF of direction g is Z_g(t) = sum_r P_g(r,t) u*_g(r), u*_g(r) = sum_i p_i(r) c_ig.
+//
+// Work layout: one thread per fluid node of the compact fluid list (no solid lanes). The
+// flow is steady, so everything that depends on it alone is prepared once by mp_init: the
+// 18-bit open-link mask of every fluid node and, for every node, (u_x, u_y, u_z, -3/2|u|^2)
+// packed in one 16-byte vector, so that a neighbour's link probability costs one load and
+// three fused multiply-adds. All species sharing the medium reuse the flow-dependent part
+// q_i of p_i = w_i (q_i + lambda/2); only lambda/2, p_a and p_d differ per species.
 #include <cmath>
 #include <cstdio>
 #include <cstring>
@@ -30,14 +37,36 @@ namespace {
 constexpr int kThreads = 256;
 constexpr int kWarps = kThreads / 32;
 constexpr int kMaxF = 4;  // density + up to three velocity moments
+constexpr uint32_t kAllLinks = (1u << 18) - 1u;
+
+// (u_x, u_y, u_z, -3/2 |u|^2) of one node, loaded as one vector
+template <typename T>
+struct alignas(4 * sizeof(T)) Flow4 {
+    T x, y, z, w;
+};
+
+// exact quotient n / d for 0 <= n < 2^31, 2 <= d < 2^31, with m = floor(2^32 / d): the
+// estimate umulhi(n, m) is floor(n/d) or one less
+struct Div {
+    unsigned d, m;
+};
+Div make_div(unsigned d) { return Div{d, (unsigned)((1ull << 32) / d)}; }
+__device__ __forceinline__ unsigned divq(unsigned n, Div v)
+{
+    unsigned q = __umulhi(n, v.m);
+    if (n - q * v.d >= v.d) ++q;
+    return q;
+}
 
 template <typename T>
 struct Args {
-    int nx, ny, nz, N, NI;
-    const uint32_t* fluid;
+    int nx, ny, nz, N, NF, NI;
+    Div dx, dxy;  // division by nx and by nx*ny
     const uint32_t* iface;
     const int32_t* ibase;
-    const T* u;  // 3*N SoA
+    const int32_t* flist;    // fluid node of each work item
+    const uint32_t* fmask;   // bit i-1: link i (inflow from r - c_i) is open
+    const Flow4<T>* u4;      // dense, zero on solid nodes
     int S, F, M;
     int dir[3];  // direction of velocity moment m (field m+1)
     T hl[MP_MAX_SPECIES];  // lambda/2
@@ -62,33 +91,52 @@ __device__ __forceinline__ bool bit_of(const uint32_t* __restrict__ w, int n)
 {
     return (__ldg(w + (n >> 5)) >> (n & 31)) & 1u;
 }
-__device__ __forceinline__ int wrap(int v, int n) { return v < 0 ? v + n : (v >= n ? v - n : v); }
 
 // Correctly rounded arithmetic the compiler may not contract or reorder. A link
 // probability is evaluated by both end nodes of the link and must come out bitwise equal,
-// so that the two ends compute exactly opposite net fluxes (the step conserves mass up to
-// the final, unbiased rounding of each node's update).
+// so that the two ends compute exactly opposite net fluxes.
 __device__ __forceinline__ float rn_mul(float a, float b) { return __fmul_rn(a, b); }
 __device__ __forceinline__ float rn_add(float a, float b) { return __fadd_rn(a, b); }
 __device__ __forceinline__ float rn_sub(float a, float b) { return __fsub_rn(a, b); }
+__device__ __forceinline__ float rn_fma(float a, float b, float c) { return __fmaf_rn(a, b, c); }
 __device__ __forceinline__ double rn_mul(double a, double b) { return __dmul_rn(a, b); }
 __device__ __forceinline__ double rn_add(double a, double b) { return __dadd_rn(a, b); }
 __device__ __forceinline__ double rn_sub(double a, double b) { return __dsub_rn(a, b); }
+__device__ __forceinline__ double rn_fma(double a, double b, double c) { return __fma_rn(a, b, c); }
 
+// e = c_i . u: a signed sum of one or two components, added in x, y, z order
 template <typename T>
-__device__ __forceinline__ T speed2(T ux, T uy, T uz)
+__device__ __forceinline__ T edot(int i, T ux, T uy, T uz)
 {
-    return rn_add(rn_add(rn_mul(ux, ux), rn_mul(uy, uy)), rn_mul(uz, uz));
+    T e = T(0);
+    bool first = true;
+    if (cx(i) != 0) {
+        e = cx(i) > 0 ? ux : -ux;
+        first = false;
+    }
+    if (cy(i) != 0) {
+        const T v = cy(i) > 0 ? uy : -uy;
+        e = first ? v : rn_add(e, v);
+        first = false;
+    }
+    if (cz(i) != 0) {
+        const T v = cz(i) > 0 ? uz : -uz;
+        e = first ? v : rn_add(e, v);
+    }
+    return e;
 }
 
-// Advective part of the link probability, w_i (3 e + 9/2 e^2 - 3/2 |u|^2), e = c_i.u
-// (f_i^eq(rho = 1, u)/rho - w_i), in a fixed sequence of correctly rounded operations.
+// flow-dependent part of p_i / w_i: q = e (3 + 9/2 e) - 3/2 |u|^2 (a = -3/2 |u|^2 stored)
 template <typename T>
-__device__ __forceinline__ T advective(int i, T ux, T uy, T uz, T uu)
+__device__ __forceinline__ T qlink(T e, T a)
 {
-    const T e = rn_add(rn_add(rn_mul(T(cx(i)), ux), rn_mul(T(cy(i)), uy)), rn_mul(T(cz(i)), uz));
-    const T q = rn_sub(rn_add(rn_mul(T(3), e), rn_mul(T(4.5), rn_mul(e, e))), rn_mul(T(1.5), uu));
-    return rn_mul(weight<T>(i), q);
+    return rn_fma(e, rn_fma(T(4.5), e, T(3)), a);
+}
+
+template <typename T>
+__device__ __forceinline__ T pick(const T v[3], int g)
+{
+    return g == 0 ? v[0] : (g == 1 ? v[1] : v[2]);
 }
 
 // What a fluid node r needs from its links. Link i is the inflow direction c_i: its source
@@ -96,50 +144,45 @@ __device__ __forceinline__ T advective(int i, T ux, T uy, T uz, T uu)
 // Both are open iff s_i is fluid.
 template <typename T>
 struct Node {
-    T cin[kQ];       // advective part of p_i at s_i (link s_i -> r)
-    T cout[kQ];      // advective part of p_opposite(i) at r (link r -> s_i)
-    int src[kQ];     // s_i, or -1 when s_i is solid
-    T UA[3], UW[3];  // sum over open outgoing links of w adv c_g, of w c_g  (u*_g)
-    T QA[3], QW[3];  // same with c_g^2 (Z(0) only)
+    T cin[kQ];    // q of link i at s_i (s_i -> r)
+    T cout[kQ];   // q of link opposite(i) at r (r -> s_i)
+    int src[kQ];  // s_i, or -1 when s_i is solid
+    int n;
     bool itf;
     int aidx;  // compact index among interfacial nodes
 };
 
-template <typename T, bool kWithQ>
-__device__ __forceinline__ void load_node(const Args<T>& a, int n, Node<T>& d)
+template <typename T>
+__device__ __forceinline__ void load_node(const Args<T>& a, int k, Node<T>& d)
 {
-    const int x = n % a.nx, y = (n / a.nx) % a.ny, z = n / (a.nx * a.ny);
-    const T ux = a.u[n], uy = a.u[a.N + n], uz = a.u[2 * a.N + n];
-    const T uu = speed2(ux, uy, uz);
-#pragma unroll
-    for (int g = 0; g < 3; ++g) d.UA[g] = d.UW[g] = d.QA[g] = d.QW[g] = T(0);
-    d.itf = false;
+    const int n = __ldg(a.flist + k);
+    const uint32_t mask = __ldg(a.fmask + k);
+    const int yz = (int)divq((unsigned)n, a.dx);
+    const int x = n - yz * a.nx;
+    const int z = (int)divq((unsigned)n, a.dxy);
+    const int y = yz - z * a.ny;
+    const int nxy = a.nx * a.ny;
+    // offsets to x-1, x+1, y-1, y+1, z-1, z+1 with periodic wrap
+    const int oxm = x == 0 ? a.nx - 1 : -1, oxp = x == a.nx - 1 ? 1 - a.nx : 1;
+    const int oym = y == 0 ? (a.ny - 1) * a.nx : -a.nx, oyp = y == a.ny - 1 ? (1 - a.ny) * a.nx : a.nx;
+    const int ozm = z == 0 ? (a.nz - 1) * nxy : -nxy, ozp = z == a.nz - 1 ? (1 - a.nz) * nxy : nxy;
+    const Flow4<T> ur = a.u4[n];
+    d.n = n;
 #pragma unroll
     for (int i = 1; i < kQ; ++i) {
-        const int s = wrap(x - cx(i), a.nx) + a.nx * (wrap(y - cy(i), a.ny) + a.ny * wrap(z - cz(i), a.nz));
-        const int o = opposite(i);
-        if (bit_of(a.fluid, s)) {
-            const T sx = a.u[s], sy = a.u[a.N + s], sz = a.u[2 * a.N + s];
-            d.cin[i] = advective<T>(i, sx, sy, sz, speed2(sx, sy, sz));
-            d.cout[i] = advective<T>(o, ux, uy, uz, uu);
+        if ((mask >> (i - 1)) & 1u) {
+            const int s = n + (cx(i) > 0 ? oxm : (cx(i) < 0 ? oxp : 0)) +
+                          (cy(i) > 0 ? oym : (cy(i) < 0 ? oyp : 0)) + (cz(i) > 0 ? ozm : (cz(i) < 0 ? ozp : 0));
+            const Flow4<T> us = a.u4[s];
+            d.cin[i] = qlink(edot<T>(i, us.x, us.y, us.z), us.w);
+            d.cout[i] = qlink(edot<T>(opposite(i), ur.x, ur.y, ur.z), ur.w);
             d.src[i] = s;
-#pragma unroll
-            for (int g = 0; g < 3; ++g) {
-                if (ci(o, g) != 0) {
-                    d.UA[g] += d.cout[i] * T(ci(o, g));
-                    d.UW[g] += weight<T>(o) * T(ci(o, g));
-                    if (kWithQ) {
-                        d.QA[g] += d.cout[i];
-                        d.QW[g] += weight<T>(o);
-                    }
-                }
-            }
         } else {
             d.cin[i] = d.cout[i] = T(0);
             d.src[i] = -1;
-            d.itf = true;
         }
     }
+    d.itf = mask != kAllLinks;
     d.aidx = 0;
     if (d.itf) {
         const uint32_t bits = __ldg(a.iface + (n >> 5));
@@ -147,10 +190,33 @@ __device__ __forceinline__ void load_node(const Args<T>& a, int n, Node<T>& d)
     }
 }
 
+// link probabilities of one species: p = w q + w lambda/2
 template <typename T>
-__device__ __forceinline__ T pick(const T v[3], int g)
+__device__ __forceinline__ void species_probs(const Node<T>& d, T hl, T (&pin)[kQ], T (&pout)[kQ])
 {
-    return g == 0 ? v[0] : (g == 1 ? v[1] : v[2]);
+    const T whl_face = rn_mul(weight<T>(1), hl), whl_edge = rn_mul(weight<T>(5), hl);
+#pragma unroll
+    for (int i = 1; i < kQ; ++i) {
+        const T whl = is_face(i) ? whl_face : whl_edge;
+        pin[i] = d.src[i] >= 0 ? rn_fma(weight<T>(i), d.cin[i], whl) : T(0);
+        pout[i] = d.src[i] >= 0 ? rn_fma(weight<T>(i), d.cout[i], whl) : T(0);
+    }
+}
+
+// u*_g(r) = sum over open outgoing links of p c_g, and sum of p c_g^2, for direction g
+template <typename T>
+__device__ __forceinline__ void mean_step(const T (&pout)[kQ], int g, T& us, T& us2)
+{
+    us = T(0);
+    us2 = T(0);
+#pragma unroll
+    for (int i = 1; i < kQ; ++i) {
+        const int c = ci(opposite(i), g);
+        if (c != 0) {
+            us += T(c) * pout[i];
+            us2 += pout[i];
+        }
+    }
 }
 
 template <typename T>
@@ -217,45 +283,45 @@ __device__ __forceinline__ bool grid_total(double* partials, int K, unsigned int
 
 // ---------------------------------------------------------------------------------------
 // Step t -> t+1 of every species and field, fused with Z_g(t+1) and D_g(t+1).
+//
+// Eq. propagated_quantity is evaluated as X(r) + sum_i J_i with the net flux of link i
+//   J_i = fl(p_i(s_i) X(s_i)) - fl(p_opp(i)(r) X(r)),
+// every factor and product correctly rounded in a fixed order. The node at the other end
+// of the link computes the same two products, so it sees exactly -J_i: the exchange is
+// antisymmetric and total mass changes only through the final rounding of each node's
+// update, which is unbiased and vanishes for a stationary field (|sum J| below half an
+// ulp). The direct form X* = inflow + stay X would instead carry the rounding of the stay
+// fraction (about 3e-8 in FP32) into every step. The sorption exchange
+// J_s = fl(p_a X) - fl(p_d X_ads) is applied the same way (Eqs. Pads and newP).
 // ---------------------------------------------------------------------------------------
 template <typename T>
 __global__ void __launch_bounds__(kThreads)
     k_step(const Args<T> a, const T* __restrict__ P, T* __restrict__ Pn, const T* __restrict__ A,
            T* __restrict__ An)
 {
-    const int n = blockIdx.x * kThreads + threadIdx.x;
-    const bool active = n < a.N && bit_of(a.fluid, n);
+    const int k = blockIdx.x * kThreads + threadIdx.x;
+    const bool active = k < a.NF;
     Node<T> d;
-    if (active) load_node<T, false>(a, n, d);
+    if (active) load_node<T>(a, k, d);
     const int K = a.S * a.M;
     for (int sp = 0; sp < a.S; ++sp) {
         const T hl = a.hl[sp], pa = a.pa[sp], pd = a.pd[sp];
         T zp[kMaxF] = {T(0), T(0), T(0), T(0)};
         if (active) {
-            // link probabilities of this species: p = advective part + w lambda/2
-            const T whl_face = rn_mul(weight<T>(1), hl), whl_edge = rn_mul(weight<T>(5), hl);
             T pin[kQ], pout[kQ];
-#pragma unroll
-            for (int i = 1; i < kQ; ++i) {
-                const T whl = is_face(i) ? whl_face : whl_edge;
-                pin[i] = rn_add(d.cin[i], whl);
-                pout[i] = rn_add(d.cout[i], whl);
-            }
+            species_probs(d, hl, pin, pout);
 #pragma unroll
             for (int f = 0; f < kMaxF; ++f) {
                 if (f < a.F) {
                     const size_t base = (size_t)(sp * a.F + f) * a.N;
                     const T* X = P + base;
-                    const T xr = __ldg(X + n);
-                    // Eq. propagated_quantity as a sum of net link fluxes
-                    // J_i = p_i(s_i) X(s_i) - p_opp(i)(r) X(r): the stay fraction never appears
+                    const T xr = __ldg(X + d.n);
                     T delta = T(0);
 #pragma unroll
                     for (int i = 1; i < kQ; ++i)
                         if (d.src[i] >= 0)
                             delta = rn_add(delta, rn_sub(rn_mul(pin[i], __ldg(X + d.src[i])), rn_mul(pout[i], xr)));
                     if (d.itf) {
-                        // Eqs. Pads, newP: exchange J_s = p_a X - p_d X_ads
                         const size_t ai = (size_t)(sp * a.F + f) * a.NI + d.aidx;
                         const T xa = A[ai];
                         const T js = rn_sub(rn_mul(pa, xr), rn_mul(pd, xa));
@@ -263,10 +329,11 @@ __global__ void __launch_bounds__(kThreads)
                         An[ai] = rn_add(xa, js);
                     }
                     const T xn = rn_add(xr, delta);
-                    Pn[base + n] = xn;
+                    Pn[base + d.n] = xn;
                     if (f >= 1) {
-                        const int g = a.dir[f - 1];
-                        zp[f - 1] = xn * (pick(d.UA, g) + hl * pick(d.UW, g));
+                        T us, us2;
+                        mean_step(pout, a.dir[f - 1], us, us2);
+                        zp[f - 1] = xn * us;
                     }
                 }
             }
@@ -280,10 +347,10 @@ __global__ void __launch_bounds__(kThreads)
     __shared__ long long s_t1;
     if (threadIdx.x == 0) s_t1 = *((volatile long long*)tdev) + 1;
     // s_t1 is only read by thread 0 of the last block, after the barriers in grid_total
-    bool last = grid_total(a.partials, K, a.ticket, [&](int k, double tot) {
+    bool last = grid_total(a.partials, K, a.ticket, [&](int kk, double tot) {
         const long long t1 = s_t1;
-        Z[(size_t)k * cap + t1] = tot;
-        D[(size_t)k * cap + t1] = D[(size_t)k * cap + t1 - 1] + tot;
+        Z[(size_t)kk * cap + t1] = tot;
+        D[(size_t)kk * cap + t1] = D[(size_t)kk * cap + t1 - 1] + tot;
     });
     if (last && threadIdx.x == 0) *tdev = s_t1;
 }
@@ -297,36 +364,36 @@ template <typename T>
 __global__ void __launch_bounds__(kThreads)
     k_init(const Args<T> a, const InitExtra b, T* __restrict__ P1, T* __restrict__ A1)
 {
-    const int n = blockIdx.x * kThreads + threadIdx.x;
-    const bool active = n < a.N && bit_of(a.fluid, n);
+    const int k = blockIdx.x * kThreads + threadIdx.x;
+    const bool active = k < a.NF;
     Node<T> d;
-    if (active) load_node<T, true>(a, n, d);
+    if (active) load_node<T>(a, k, d);
     const int K2 = 2 * a.S * a.M;
     for (int sp = 0; sp < a.S; ++sp) {
         const T hl = a.hl[sp], pa = a.pa[sp], pd = a.pd[sp];
         const T invZ = (T)b.invZ[sp];
         T zp[2 * kMaxF] = {T(0), T(0), T(0), T(0), T(0), T(0), T(0), T(0)};
         if (active) {
-            T out = T(0);
+            T pin[kQ], pout[kQ];
+            species_probs(d, hl, pin, pout);
+            T out = T(0), inw = T(0);
 #pragma unroll
-            for (int i = 1; i < kQ; ++i)
-                if (d.src[i] >= 0) out += d.cout[i] + weight<T>(i) * hl;
+            for (int i = 1; i < kQ; ++i) {
+                out += pout[i];
+                inw += pin[i];
+            }
             const T stay = T(1) - out - (d.itf ? pa : T(0));
             // density field: X0 uniform over the free fluid (1/N_f or the free weight 1/Z),
             // adsorbed K/Z on the interface for the equilibrium start
             const T x0 = b.uniform ? (T)b.inv_nf : invZ;
             const T xa0 = (b.uniform || !d.itf) ? T(0) : (T)b.K[sp] * invZ;
-            T inflow = T(0);
-#pragma unroll
-            for (int i = 1; i < kQ; ++i)
-                if (d.src[i] >= 0) inflow += (d.cin[i] + weight<T>(i) * hl) * x0;
-            T xn = inflow + stay * x0;
+            T xn = inw * x0 + stay * x0;
             if (d.itf) {
                 const size_t ai = (size_t)(sp * a.F) * a.NI + d.aidx;
                 xn += pd * xa0;
                 A1[ai] = pa * x0 + (T(1) - pd) * xa0;
             }
-            P1[(size_t)(sp * a.F) * a.N + n] = xn;
+            P1[(size_t)(sp * a.F) * a.N + d.n] = xn;
 #pragma unroll
             for (int m = 0; m < kMaxF - 1; ++m) {
                 if (m < a.M) {
@@ -334,12 +401,14 @@ __global__ void __launch_bounds__(kThreads)
                     T pg = T(0);
 #pragma unroll
                     for (int i = 1; i < kQ; ++i)
-                        if (d.src[i] >= 0 && ci(i, g) != 0)
-                            pg += (d.cin[i] + weight<T>(i) * hl) * T(ci(i, g)) * invZ;
-                    P1[(size_t)(sp * a.F + 1 + m) * a.N + n] = pg;
+                        if (ci(i, g) != 0) pg += pin[i] * T(ci(i, g));
+                    pg *= invZ;
+                    P1[(size_t)(sp * a.F + 1 + m) * a.N + d.n] = pg;
                     if (d.itf) A1[(size_t)(sp * a.F + 1 + m) * a.NI + d.aidx] = T(0);
-                    zp[2 * m] = invZ * (pick(d.QA, g) + hl * pick(d.QW, g));
-                    zp[2 * m + 1] = pg * (pick(d.UA, g) + hl * pick(d.UW, g));
+                    T us, us2;
+                    mean_step(pout, g, us, us2);
+                    zp[2 * m] = invZ * us2;
+                    zp[2 * m + 1] = pg * us;
                 }
             }
         }
@@ -348,9 +417,9 @@ __global__ void __launch_bounds__(kThreads)
     const long long cap = a.cap;
     double* Z = a.Z;
     double* D = a.D;
-    bool last = grid_total(a.partials, K2, a.ticket, [&](int k, double tot) {
-        const int series = k / 2;
-        if ((k & 1) == 0) {
+    bool last = grid_total(a.partials, K2, a.ticket, [&](int kk, double tot) {
+        const int series = kk / 2;
+        if ((kk & 1) == 0) {
             Z[(size_t)series * cap + 0] = tot;
             D[(size_t)series * cap + 0] = tot / 2.0;
         } else {
@@ -361,32 +430,26 @@ __global__ void __launch_bounds__(kThreads)
     if (last && threadIdx.x == 0) *a.tdev = 1;
 }
 
-// Count open links with p_i < 0 and nodes with a negative stay fraction, per species.
+// Count open links with p_i < 0 and nodes with a negative stay fraction, over species.
 template <typename T>
 __global__ void __launch_bounds__(kThreads)
     k_negative(const Args<T> a, unsigned long long* __restrict__ counts)
 {
-    const int n = blockIdx.x * kThreads + threadIdx.x;
-    if (n >= a.N || !bit_of(a.fluid, n)) return;
-    const int x = n % a.nx, y = (n / a.nx) % a.ny, z = n / (a.nx * a.ny);
-    const T ux = a.u[n], uy = a.u[a.N + n], uz = a.u[2 * a.N + n];
-    const T uu = ux * ux + uy * uy + uz * uz;
+    const int k = blockIdx.x * kThreads + threadIdx.x;
+    if (k >= a.NF) return;
+    Node<T> d;
+    load_node<T>(a, k, d);
     for (int sp = 0; sp < a.S; ++sp) {
+        T pin[kQ], pout[kQ];
+        species_probs(d, a.hl[sp], pin, pout);
         unsigned neg = 0;
         T out = T(0);
-        bool itf = false;
 #pragma unroll
         for (int i = 1; i < kQ; ++i) {
-            const int t = wrap(x + cx(i), a.nx) + a.nx * (wrap(y + cy(i), a.ny) + a.ny * wrap(z + cz(i), a.nz));
-            if (bit_of(a.fluid, t)) {
-                const T p = advective<T>(i, ux, uy, uz, uu) + weight<T>(i) * a.hl[sp];
-                neg += p < T(0);
-                out += p;
-            } else {
-                itf = true;
-            }
+            neg += (d.src[i] >= 0 && pout[i] < T(0)) ? 1u : 0u;
+            out += pout[i];
         }
-        const T stay = T(1) - out - (itf ? a.pa[sp] : T(0));
+        const T stay = T(1) - out - (d.itf ? a.pa[sp] : T(0));
         if (neg) atomicAdd(&counts[0], (unsigned long long)neg);
         if (stay < T(0)) atomicAdd(&counts[1], 1ull);
     }
@@ -398,14 +461,15 @@ template <typename T>
 __global__ void __launch_bounds__(kThreads)
     k_mass(const Args<T> a, const T* __restrict__ P, const T* __restrict__ A, double* __restrict__ out)
 {
-    const int n = blockIdx.x * kThreads + threadIdx.x;
+    const int k = blockIdx.x * kThreads + threadIdx.x;
     double v[3] = {0.0, 0.0, 0.0};
-    if (n < a.N && bit_of(a.fluid, n)) {
+    if (k < a.NF) {
+        const int n = __ldg(a.flist + k);
         v[0] = (double)P[n];
         const uint32_t bits = __ldg(a.iface + (n >> 5));
         if ((bits >> (n & 31)) & 1u) {
-            const int k = __ldg(a.ibase + (n >> 5)) + __popc(bits & ((1u << (n & 31)) - 1u));
-            v[1] = (double)A[k];
+            const int j = __ldg(a.ibase + (n >> 5)) + __popc(bits & ((1u << (n & 31)) - 1u));
+            v[1] = (double)A[j];
             v[2] = v[0];
         }
     }
@@ -419,19 +483,46 @@ __global__ void __launch_bounds__(kThreads)
     __syncthreads();
     if (threadIdx.x < 3) {
         double t = 0.0;
-        for (int k = 0; k < kWarps; ++k) t += s[threadIdx.x][k];
+        for (int q = 0; q < kWarps; ++q) t += s[threadIdx.x][q];
         out[(size_t)blockIdx.x * 3 + threadIdx.x] = t;
     }
 }
 
+// Static flow data: Flow4 of every node (zero on solids) and the open mask of every fluid
+// node. -3/2 |u|^2 is computed here once, so both ends of a link read the same value.
 template <typename T>
-__global__ void k_convert_u(const float* __restrict__ in, T* __restrict__ out, const uint32_t* __restrict__ fluid,
-                            int N)
+__global__ void k_pack_flow(const float* __restrict__ in, const uint32_t* __restrict__ fluid, int N,
+                            Flow4<T>* __restrict__ u4)
 {
-    int k = blockIdx.x * blockDim.x + threadIdx.x;
-    if (k >= 3 * N) return;
-    int n = k % N;
-    out[k] = (in && bit_of(fluid, n)) ? (T)in[k] : T(0);
+    const int n = blockIdx.x * blockDim.x + threadIdx.x;
+    if (n >= N) return;
+    Flow4<T> v{T(0), T(0), T(0), T(0)};
+    if (in && bit_of(fluid, n)) {
+        v.x = (T)in[n];
+        v.y = (T)in[N + n];
+        v.z = (T)in[2 * N + n];
+        v.w = rn_mul(T(-1.5), rn_add(rn_add(rn_mul(v.x, v.x), rn_mul(v.y, v.y)), rn_mul(v.z, v.z)));
+    }
+    u4[n] = v;
+}
+
+__global__ void k_open_mask(const int32_t* __restrict__ flist, const uint32_t* __restrict__ fluid, int NF,
+                            int nx, int ny, int nz, uint32_t* __restrict__ fmask)
+{
+    const int k = blockIdx.x * blockDim.x + threadIdx.x;
+    if (k >= NF) return;
+    const int n = flist[k];
+    const int x = n % nx, y = (n / nx) % ny, z = n / (nx * ny);
+    uint32_t m = 0;
+#pragma unroll
+    for (int i = 1; i < kQ; ++i) {
+        int xs = x - cx(i), ys = y - cy(i), zs = z - cz(i);
+        xs = xs < 0 ? xs + nx : (xs >= nx ? xs - nx : xs);
+        ys = ys < 0 ? ys + ny : (ys >= ny ? ys - ny : ys);
+        zs = zs < 0 ? zs + nz : (zs >= nz ? zs - nz : zs);
+        if (bit_of(fluid, xs + nx * (ys + ny * zs))) m |= 1u << (i - 1);
+    }
+    fmask[k] = m;
 }
 
 }  // namespace
@@ -448,7 +539,8 @@ struct mp_ctx {
     long long cap = 0;
     long long t = 0;
     double Db[MP_MAX_SPECIES], ka[MP_MAX_SPECIES], kd[MP_MAX_SPECIES];
-    void* u = nullptr;
+    void* u4 = nullptr;          // Flow4<T> per node
+    uint32_t* fmask = nullptr;   // open-link mask per fluid node
     void* P[2] = {nullptr, nullptr};
     void* A[2] = {nullptr, nullptr};
     int cur = 0;
@@ -474,11 +566,15 @@ Args<T> make_args(const mp_ctx* c)
     a.ny = c->geo.ny;
     a.nz = c->geo.nz;
     a.N = c->geo.N;
+    a.NF = (int)c->geo.n_fluid;
     a.NI = (int)c->geo.n_iface;
-    a.fluid = c->geo.fluid;
+    a.dx = make_div((unsigned)c->geo.nx);
+    a.dxy = make_div((unsigned)(c->geo.nx * c->geo.ny));
     a.iface = c->geo.iface;
     a.ibase = c->geo.ibase;
-    a.u = (const T*)c->u;
+    a.flist = c->geo.flist;
+    a.fmask = c->fmask;
+    a.u4 = (const Flow4<T>*)c->u4;
     a.S = c->S;
     a.F = c->F;
     a.M = c->M;
@@ -501,7 +597,8 @@ void destroy(mp_ctx* c)
 {
     if (!c) return;
     free_geometry(&c->geo, nullptr, false);
-    cudaFree(c->u);
+    cudaFree(c->u4);
+    cudaFree(c->fmask);
     for (int b = 0; b < 2; ++b) {
         cudaFree(c->P[b]);
         cudaFree(c->A[b]);
@@ -523,8 +620,9 @@ int init_typed(mp_ctx* c, const float* u_in, int init_density)
     const size_t fieldA = (size_t)c->S * c->F * NI;
     const int Kser = c->S * c->M;
     c->elem = sizeof(T);
-    c->blocks = (N + kThreads - 1) / kThreads;
-    MP_CUDA(cudaMalloc(&c->u, sizeof(T) * 3 * (size_t)N));
+    c->blocks = (int)((c->geo.n_fluid + kThreads - 1) / kThreads);
+    MP_CUDA(cudaMalloc(&c->u4, sizeof(Flow4<T>) * (size_t)N));
+    MP_CUDA(cudaMalloc(&c->fmask, sizeof(uint32_t) * (size_t)c->geo.n_fluid));
     for (int b = 0; b < 2; ++b) {
         MP_CUDA(cudaMalloc(&c->P[b], sizeof(T) * fieldN));
         MP_CUDA(cudaMalloc(&c->A[b], sizeof(T) * fieldA));
@@ -542,7 +640,9 @@ int init_typed(mp_ctx* c, const float* u_in, int init_density)
     MP_CUDA(cudaMalloc(&c->partials, sizeof(double) * (size_t)c->blocks * per_block));
     MP_CUDA(cudaMalloc(&c->ticket, sizeof(unsigned int)));
     MP_CUDA(cudaMemsetAsync(c->ticket, 0, sizeof(unsigned int), c->stream));
-    k_convert_u<T><<<(3 * N + 255) / 256, 256, 0, c->stream>>>(u_in, (T*)c->u, c->geo.fluid, N);
+    k_pack_flow<T><<<(N + 255) / 256, 256, 0, c->stream>>>(u_in, c->geo.fluid, N, (Flow4<T>*)c->u4);
+    k_open_mask<<<c->blocks, kThreads, 0, c->stream>>>(c->geo.flist, c->geo.fluid, (int)c->geo.n_fluid,
+                                                        c->geo.nx, c->geo.ny, c->geo.nz, c->fmask);
     MP_CUDA(cudaGetLastError());
 
     Args<T> a = make_args<T>(c);
