@@ -183,6 +183,42 @@ int mp_set_field(mp_ctx* c, int species, int field, const double* free_dense,
 int mp_classify(const mp_geometry* g, uint8_t* cls, int64_t* n_fluid, int64_t* n_interface,
                 int64_t* n_cluster, void* stream);
 
+/*
+ * mp_step_noalloc -- one moment-propagation + sorption step of one propagated field of one
+ * species, on caller-owned dense device arrays, that allocates no memory of any kind (no
+ * cudaMalloc, no cudaFree, no allocating library routine). It serves callers that cannot
+ * allocate device memory themselves or let a library do so: code running inside a host
+ * application that owns every device allocation (a fixed budget or its own memory pool),
+ * or code that must avoid the implicit device synchronisation of cudaMalloc/cudaFree.
+ * The paper has no counterpart; the update is the same as mp_step's (same readings, same
+ * rounding of link probabilities), recomputed from the solid mask and u on every call.
+ *
+ *  nx, ny, nz    lattice (each >= 3); N = nx*ny*nz must not exceed 2,097,152 nodes: the
+ *                step's FP64 reduction uses a fixed scratch array of 8192 block partials
+ *                (64 KiB plus a counter, a __device__ array that every GPU using this entry
+ *                point keeps until the library is unloaded). Larger N returns MP_EINVAL.
+ *  solid         device, N bytes, nonzero = solid.
+ *  u             device, FP32 3*N SoA, or NULL (rest).
+ *  D_b, k_a, k_d as for mp_init.
+ *  direction     0, 1, 2: Z_out = sum_r X_out(r) u*_g(r) (the VACF term of a velocity
+ *                moment); -1: Z_out = sum_r X_out(r) (the free mass).
+ *  X, X_ads      device, FP32, N each: the field and its adsorbed partner (dense; X_ads is
+ *                read on interfacial nodes only).
+ *  X_out, X_ads_out  device, FP32, N each, written everywhere (zero on solid nodes, X_ads_out
+ *                zero off the interface); must not alias the inputs.
+ *  Z_out         device, one double, written when the step completes.
+ *  stream        cudaStream_t or NULL. Asynchronous.
+ * The first call on a device looks up the scratch array's device address (once, with that
+ * device current); make that first call before any stream capture. Every call shares the
+ * one scratch array and leaves its contents behind: the counter is cleared by each call, so
+ * calls that overlap on the GPU (different streams, concurrent host threads) race and must
+ * be serialised by the caller.
+ * Errors: MP_EINVAL, MP_ECUDA.
+ */
+int mp_step_noalloc(int nx, int ny, int nz, const uint8_t* solid, const float* u, double D_b,
+                    double k_a, double k_d, int direction, const float* X, const float* X_ads,
+                    float* X_out, float* X_ads_out, double* Z_out, void* stream);
+
 /* mp_free -- release a context and all its device memory (NULL is accepted). */
 void mp_free(mp_ctx* c);
 

@@ -73,8 +73,10 @@ _lib.lb_steady.argtypes = [ctypes.POINTER(mp_geometry), _dp, _c_dbl, _c_dbl, _c_
                            _c_vp, ctypes.POINTER(_c_i64), _dp, _c_vp]
 _lib.mp_classify.argtypes = [ctypes.POINTER(mp_geometry), _c_vp, ctypes.POINTER(_c_i64),
                              ctypes.POINTER(_c_i64), ctypes.POINTER(_c_i64), _c_vp]
+_lib.mp_step_noalloc.argtypes = [_c_int, _c_int, _c_int, _c_vp, _c_vp, _c_dbl, _c_dbl, _c_dbl, _c_int,
+                                 _c_vp, _c_vp, _c_vp, _c_vp, _c_vp, _c_vp]
 for _f in ("mp_init", "mp_init_batch", "mp_step", "mp_vacf", "mp_mass", "mp_info", "mp_get_field",
-           "mp_set_field", "lb_steady", "mp_classify"):
+           "mp_set_field", "lb_steady", "mp_classify", "mp_step_noalloc"):
     getattr(_lib, _f).restype = _c_int
 
 
@@ -247,6 +249,17 @@ def mp_classify(solid, stream=None):
                             ctypes.byref(nc), _stream(stream)))
     del keep
     return cls, (nf.value, ni.value, nc.value)
+
+
+def mp_step_noalloc(solid, u, D_b, k_a, k_d, direction, X, X_ads, X_out, X_ads_out, Z_out,
+                    stream=None):
+    """mp_step_noalloc of include/mp.h: one step of one field on caller-owned device arrays
+    (torch CUDA tensors), allocating nothing. solid: uint8 (nz, ny, nx); u: FP32 (3, nz, ny,
+    nx) or None; X, X_ads, X_out, X_ads_out: FP32 (nz, ny, nx); Z_out: one FP64 element."""
+    nz, ny, nx = solid.shape
+    _check(_lib.mp_step_noalloc(nx, ny, nz, _addr(solid), _addr(u), float(D_b), float(k_a), float(k_d),
+                                int(direction), _addr(X), _addr(X_ads), _addr(X_out), _addr(X_ads_out),
+                                _addr(Z_out), _stream(stream)))
 
 
 def mp_free(ctx: Context):
