@@ -59,9 +59,16 @@ __device__ __forceinline__ unsigned divq(unsigned n, Div v)
     return q;
 }
 
+// all propagated fields of one node and species, stored together (padded to 2 or 4)
+template <typename T, int FP>
+struct alignas(FP * sizeof(T)) FieldVec {
+    T v[FP];
+};
+
 template <typename T>
 struct Args {
     int nx, ny, nz, N, NF, NI;
+    int FP;  // padded field count of the [species][node][field] layout: 2 or 4
     Div dx, dxy;  // division by nx and by nx*ny
     const uint32_t* iface;
     const int32_t* ibase;
@@ -99,6 +106,37 @@ __device__ __forceinline__ T pick(const T v[3], int g)
     return g == 0 ? v[0] : (g == 1 ? v[1] : v[2]);
 }
 
+// Periodic neighbourhood of a node: offsets to x-1, x+1, y-1, y+1, z-1, z+1.
+struct Nbr {
+    int n, oxm, oxp, oym, oyp, ozm, ozp;
+};
+
+template <typename T>
+__device__ __forceinline__ Nbr node_nbrs(const Args<T>& a, int n)
+{
+    Nbr b;
+    const int yz = (int)divq((unsigned)n, a.dx);
+    const int x = n - yz * a.nx;
+    const int z = (int)divq((unsigned)n, a.dxy);
+    const int y = yz - z * a.ny;
+    const int nxy = a.nx * a.ny;
+    b.n = n;
+    b.oxm = x == 0 ? a.nx - 1 : -1;
+    b.oxp = x == a.nx - 1 ? 1 - a.nx : 1;
+    b.oym = y == 0 ? (a.ny - 1) * a.nx : -a.nx;
+    b.oyp = y == a.ny - 1 ? (1 - a.ny) * a.nx : a.nx;
+    b.ozm = z == 0 ? (a.nz - 1) * nxy : -nxy;
+    b.ozp = z == a.nz - 1 ? (1 - a.nz) * nxy : nxy;
+    return b;
+}
+
+// s_i = r - c_i
+__device__ __forceinline__ int src_of(const Nbr& b, int i)
+{
+    return b.n + (cx(i) > 0 ? b.oxm : (cx(i) < 0 ? b.oxp : 0)) + (cy(i) > 0 ? b.oym : (cy(i) < 0 ? b.oyp : 0)) +
+           (cz(i) > 0 ? b.ozm : (cz(i) < 0 ? b.ozp : 0));
+}
+
 // What a fluid node r needs from its links. Link i is the inflow direction c_i: its source
 // is s_i = r - c_i, and the reverse link (opposite(i), from r to s_i) carries the outflow.
 // Both are open iff s_i is fluid.
@@ -113,26 +151,24 @@ struct Node {
 };
 
 template <typename T>
+__device__ __forceinline__ int iface_index(const Args<T>& a, int n)
+{
+    const uint32_t bits = __ldg(a.iface + (n >> 5));
+    return __ldg(a.ibase + (n >> 5)) + __popc(bits & ((1u << (n & 31)) - 1u));
+}
+
+template <typename T>
 __device__ __forceinline__ void load_node(const Args<T>& a, int k, Node<T>& d)
 {
     const int n = __ldg(a.flist + k);
     const uint32_t mask = __ldg(a.fmask + k);
-    const int yz = (int)divq((unsigned)n, a.dx);
-    const int x = n - yz * a.nx;
-    const int z = (int)divq((unsigned)n, a.dxy);
-    const int y = yz - z * a.ny;
-    const int nxy = a.nx * a.ny;
-    // offsets to x-1, x+1, y-1, y+1, z-1, z+1 with periodic wrap
-    const int oxm = x == 0 ? a.nx - 1 : -1, oxp = x == a.nx - 1 ? 1 - a.nx : 1;
-    const int oym = y == 0 ? (a.ny - 1) * a.nx : -a.nx, oyp = y == a.ny - 1 ? (1 - a.ny) * a.nx : a.nx;
-    const int ozm = z == 0 ? (a.nz - 1) * nxy : -nxy, ozp = z == a.nz - 1 ? (1 - a.nz) * nxy : nxy;
+    const Nbr b = node_nbrs(a, n);
     const Flow4<T> ur = a.u4[n];
     d.n = n;
 #pragma unroll
     for (int i = 1; i < kQ; ++i) {
         if ((mask >> (i - 1)) & 1u) {
-            const int s = n + (cx(i) > 0 ? oxm : (cx(i) < 0 ? oxp : 0)) +
-                          (cy(i) > 0 ? oym : (cy(i) < 0 ? oyp : 0)) + (cz(i) > 0 ? ozm : (cz(i) < 0 ? ozp : 0));
+            const int s = src_of(b, i);
             const Flow4<T> us = a.u4[s];
             d.cin[i] = qlink(edot<T>(i, us.x, us.y, us.z), us.w);
             d.cout[i] = qlink(edot<T>(opposite(i), ur.x, ur.y, ur.z), ur.w);
@@ -143,11 +179,7 @@ __device__ __forceinline__ void load_node(const Args<T>& a, int k, Node<T>& d)
         }
     }
     d.itf = mask != kAllLinks;
-    d.aidx = 0;
-    if (d.itf) {
-        const uint32_t bits = __ldg(a.iface + (n >> 5));
-        d.aidx = __ldg(a.ibase + (n >> 5)) + __popc(bits & ((1u << (n & 31)) - 1u));
-    }
+    d.aidx = d.itf ? iface_index(a, n) : 0;
 }
 
 // link probabilities of one species: p = w q + w lambda/2
@@ -253,52 +285,149 @@ __device__ __forceinline__ bool grid_total(double* partials, int K, unsigned int
 // ulp). The direct form X* = inflow + stay X would instead carry the rounding of the stay
 // fraction (about 3e-8 in FP32) into every step. The sorption exchange
 // J_s = fl(p_a X) - fl(p_d X_ads) is applied the same way (Eqs. Pads and newP).
+//
+// All FP fields of a node are one vector, so a neighbour costs one flow load and one
+// field load. With one species the link loop consumes each neighbour at once (few live
+// registers); with several, the flow-dependent parts of the 18 links are kept in registers
+// and reused by every species. Each warp reduces its Z terms with shuffles into shared
+// memory; the block combines them after one barrier.
 // ---------------------------------------------------------------------------------------
-template <typename T>
+template <typename T, int FP, bool kSingle>
 __global__ void __launch_bounds__(kThreads)
     k_step(const Args<T> a, const T* __restrict__ P, T* __restrict__ Pn, const T* __restrict__ A,
            T* __restrict__ An)
 {
+    using V = FieldVec<T, FP>;
+    const V* __restrict__ Pv = reinterpret_cast<const V*>(P);
+    V* __restrict__ Pnv = reinterpret_cast<V*>(Pn);
+    const V* __restrict__ Av = reinterpret_cast<const V*>(A);
+    V* __restrict__ Anv = reinterpret_cast<V*>(An);
+    __shared__ double s_part[kWarps][MP_MAX_SPECIES * (kMaxF - 1)];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const int k = blockIdx.x * kThreads + threadIdx.x;
     const bool active = k < a.NF;
-    Node<T> d;
-    if (active) load_node<T>(a, k, d);
     const int K = a.S * a.M;
-    for (int sp = 0; sp < a.S; ++sp) {
-        const T hl = a.hl[sp], pa = a.pa[sp], pd = a.pd[sp];
-        T zp[kMaxF] = {T(0), T(0), T(0), T(0)};
+
+    if (kSingle) {
+        const T hl = a.hl[0], pa = a.pa[0], pd = a.pd[0];
+        T zv[kMaxF - 1] = {T(0), T(0), T(0)};
         if (active) {
-            T pin[kQ], pout[kQ];
-            species_probs(d, hl, pin, pout);
+            const int n = __ldg(a.flist + k);
+            const uint32_t mask = __ldg(a.fmask + k);
+            const Nbr b = node_nbrs(a, n);
+            const Flow4<T> ur = a.u4[n];
+            const V xr = Pv[n];
+            const T whl_face = rn_mul(weight<T>(1), hl), whl_edge = rn_mul(weight<T>(5), hl);
+            T delta[FP];
 #pragma unroll
-            for (int f = 0; f < kMaxF; ++f) {
-                if (f < a.F) {
-                    const size_t base = (size_t)(sp * a.F + f) * a.N;
-                    const T* X = P + base;
-                    const T xr = __ldg(X + d.n);
-                    T delta = T(0);
+            for (int f = 0; f < FP; ++f) delta[f] = T(0);
+            T us[3] = {T(0), T(0), T(0)};
 #pragma unroll
-                    for (int i = 1; i < kQ; ++i)
-                        if (d.src[i] >= 0)
-                            delta = rn_add(delta, rn_sub(rn_mul(pin[i], __ldg(X + d.src[i])), rn_mul(pout[i], xr)));
-                    if (d.itf) {
-                        const size_t ai = (size_t)(sp * a.F + f) * a.NI + d.aidx;
-                        const T xa = A[ai];
-                        const T js = rn_sub(rn_mul(pa, xr), rn_mul(pd, xa));
-                        delta = rn_sub(delta, js);
-                        An[ai] = rn_add(xa, js);
+            for (int i = 1; i < kQ; ++i) {
+                if ((mask >> (i - 1)) & 1u) {
+                    const int s = src_of(b, i);
+                    const Flow4<T> uf = a.u4[s];
+                    const V xs = Pv[s];
+                    const T whl = is_face(i) ? whl_face : whl_edge;
+                    const T pin = rn_fma(weight<T>(i), qlink(edot<T>(i, uf.x, uf.y, uf.z), uf.w), whl);
+                    const T pout = rn_fma(weight<T>(i), qlink(edot<T>(opposite(i), ur.x, ur.y, ur.z), ur.w), whl);
+#pragma unroll
+                    for (int f = 0; f < FP; ++f)
+                        delta[f] = rn_add(delta[f], rn_sub(rn_mul(pin, xs.v[f]), rn_mul(pout, xr.v[f])));
+#pragma unroll
+                    for (int g = 0; g < 3; ++g)
+                        if (ci(opposite(i), g) != 0) us[g] += T(ci(opposite(i), g)) * pout;
+                }
+            }
+            if (mask != kAllLinks) {
+                const int ai = iface_index(a, n);
+                const V xa = Av[ai];
+                V xan;
+#pragma unroll
+                for (int f = 0; f < FP; ++f) {
+                    const T js = rn_sub(rn_mul(pa, xr.v[f]), rn_mul(pd, xa.v[f]));
+                    delta[f] = rn_sub(delta[f], js);
+                    xan.v[f] = rn_add(xa.v[f], js);
+                }
+                Anv[ai] = xan;
+            }
+            V xn;
+#pragma unroll
+            for (int f = 0; f < FP; ++f) xn.v[f] = rn_add(xr.v[f], delta[f]);
+            Pnv[n] = xn;
+#pragma unroll
+            for (int m = 0; m < kMaxF - 1; ++m)
+                if (m < a.M && 1 + m < FP) zv[m] = xn.v[(1 + m) < FP ? 1 + m : 0] * pick(us, a.dir[m]);
+        }
+#pragma unroll
+        for (int m = 0; m < kMaxF - 1; ++m) {
+            if (m < a.M) {
+                const T w = warp_sum(zv[m]);
+                if (lane == 0) s_part[warp][m] = (double)w;
+            }
+        }
+    } else {
+        Node<T> d;
+        if (active) load_node<T>(a, k, d);
+        for (int sp = 0; sp < a.S; ++sp) {
+            const T hl = a.hl[sp], pa = a.pa[sp], pd = a.pd[sp];
+            T zv[kMaxF - 1] = {T(0), T(0), T(0)};
+            if (active) {
+                T pin[kQ], pout[kQ];
+                species_probs(d, hl, pin, pout);
+                const V* Ps = Pv + (size_t)sp * a.N;
+                const V xr = Ps[d.n];
+                T delta[FP];
+#pragma unroll
+                for (int f = 0; f < FP; ++f) delta[f] = T(0);
+#pragma unroll
+                for (int i = 1; i < kQ; ++i) {
+                    if (d.src[i] >= 0) {
+                        const V xs = Ps[d.src[i]];
+#pragma unroll
+                        for (int f = 0; f < FP; ++f)
+                            delta[f] = rn_add(delta[f], rn_sub(rn_mul(pin[i], xs.v[f]), rn_mul(pout[i], xr.v[f])));
                     }
-                    const T xn = rn_add(xr, delta);
-                    Pn[base + d.n] = xn;
-                    if (f >= 1) {
+                }
+                if (d.itf) {
+                    const size_t ai = (size_t)sp * a.NI + d.aidx;
+                    const V xa = Av[ai];
+                    V xan;
+#pragma unroll
+                    for (int f = 0; f < FP; ++f) {
+                        const T js = rn_sub(rn_mul(pa, xr.v[f]), rn_mul(pd, xa.v[f]));
+                        delta[f] = rn_sub(delta[f], js);
+                        xan.v[f] = rn_add(xa.v[f], js);
+                    }
+                    Anv[ai] = xan;
+                }
+                V xn;
+#pragma unroll
+                for (int f = 0; f < FP; ++f) xn.v[f] = rn_add(xr.v[f], delta[f]);
+                Pnv[(size_t)sp * a.N + d.n] = xn;
+#pragma unroll
+                for (int m = 0; m < kMaxF - 1; ++m) {
+                    if (m < a.M && 1 + m < FP) {
                         T us, us2;
-                        mean_step(pout, a.dir[f - 1], us, us2);
-                        zp[f - 1] = xn * us;
+                        mean_step(pout, a.dir[m], us, us2);
+                        zv[m] = xn.v[(1 + m) < FP ? 1 + m : 0] * us;
                     }
                 }
             }
+#pragma unroll
+            for (int m = 0; m < kMaxF - 1; ++m) {
+                if (m < a.M) {
+                    const T w = warp_sum(zv[m]);
+                    if (lane == 0) s_part[warp][sp * a.M + m] = (double)w;
+                }
+            }
         }
-        block_sum_store<T, kMaxF>(zp, a.M, a.partials + (size_t)blockIdx.x * K + sp * a.M);
+    }
+    __syncthreads();
+    for (int j = threadIdx.x; j < K; j += kThreads) {
+        double t = 0.0;
+        for (int w = 0; w < kWarps; ++w) t += s_part[w][j];
+        a.partials[(size_t)blockIdx.x * K + j] = t;
     }
     const long long cap = a.cap;
     double* Z = a.Z;
@@ -349,11 +478,11 @@ __global__ void __launch_bounds__(kThreads)
             const T xa0 = (b.uniform || !d.itf) ? T(0) : (T)b.K[sp] * invZ;
             T xn = inw * x0 + stay * x0;
             if (d.itf) {
-                const size_t ai = (size_t)(sp * a.F) * a.NI + d.aidx;
+                const size_t ai = ((size_t)sp * a.NI + d.aidx) * a.FP;
                 xn += pd * xa0;
                 A1[ai] = pa * x0 + (T(1) - pd) * xa0;
             }
-            P1[(size_t)(sp * a.F) * a.N + d.n] = xn;
+            P1[((size_t)sp * a.N + d.n) * a.FP] = xn;
 #pragma unroll
             for (int m = 0; m < kMaxF - 1; ++m) {
                 if (m < a.M) {
@@ -363,8 +492,8 @@ __global__ void __launch_bounds__(kThreads)
                     for (int i = 1; i < kQ; ++i)
                         if (ci(i, g) != 0) pg += pin[i] * T(ci(i, g));
                     pg *= invZ;
-                    P1[(size_t)(sp * a.F + 1 + m) * a.N + d.n] = pg;
-                    if (d.itf) A1[(size_t)(sp * a.F + 1 + m) * a.NI + d.aidx] = T(0);
+                    P1[((size_t)sp * a.N + d.n) * a.FP + 1 + m] = pg;
+                    if (d.itf) A1[((size_t)sp * a.NI + d.aidx) * a.FP + 1 + m] = T(0);
                     T us, us2;
                     mean_step(pout, g, us, us2);
                     zp[2 * m] = invZ * us2;
@@ -425,11 +554,11 @@ __global__ void __launch_bounds__(kThreads)
     double v[3] = {0.0, 0.0, 0.0};
     if (k < a.NF) {
         const int n = __ldg(a.flist + k);
-        v[0] = (double)P[n];
+        v[0] = (double)P[(size_t)n * a.FP];
         const uint32_t bits = __ldg(a.iface + (n >> 5));
         if ((bits >> (n & 31)) & 1u) {
             const int j = __ldg(a.ibase + (n >> 5)) + __popc(bits & ((1u << (n & 31)) - 1u));
-            v[1] = (double)A[j];
+            v[1] = (double)A[(size_t)j * a.FP];
             v[2] = v[0];
         }
     }
@@ -513,6 +642,7 @@ struct mp_ctx {
     long long n_neg_links = 0, n_neg_stay = 0;
     std::vector<int32_t> ilist;
     size_t elem = 4;
+    int FP = 2;  // fields per node in the [species][node][field] layout (F padded to 2 or 4)
 };
 
 namespace {
@@ -528,6 +658,7 @@ Args<T> make_args(const mp_ctx* c)
     a.N = c->geo.N;
     a.NF = (int)c->geo.n_fluid;
     a.NI = (int)c->geo.n_iface;
+    a.FP = c->FP;
     a.dx = make_div((unsigned)c->geo.nx);
     a.dxy = make_div((unsigned)(c->geo.nx * c->geo.ny));
     a.iface = c->geo.iface;
@@ -576,8 +707,9 @@ int init_typed(mp_ctx* c, const float* u_in, int init_density)
 {
     const int N = c->geo.N;
     const size_t NI = (size_t)(c->geo.n_iface > 0 ? c->geo.n_iface : 1);
-    const size_t fieldN = (size_t)c->S * c->F * N;
-    const size_t fieldA = (size_t)c->S * c->F * NI;
+    c->FP = c->F <= 2 ? 2 : 4;
+    const size_t fieldN = (size_t)c->S * N * c->FP;
+    const size_t fieldA = (size_t)c->S * NI * c->FP;
     const int Kser = c->S * c->M;
     c->elem = sizeof(T);
     c->blocks = (int)((c->geo.n_fluid + kThreads - 1) / kThreads);
@@ -645,10 +777,12 @@ template <typename T>
 int step_typed(mp_ctx* c, long long n)
 {
     Args<T> a = make_args<T>(c);
+    auto kern = c->FP == 2 ? (c->S == 1 ? k_step<T, 2, true> : k_step<T, 2, false>)
+                           : (c->S == 1 ? k_step<T, 4, true> : k_step<T, 4, false>);
     for (long long k = 0; k < n; ++k) {
         const int s = c->cur;
-        k_step<T><<<c->blocks, kThreads, 0, c->stream>>>(a, (const T*)c->P[s], (T*)c->P[1 - s],
-                                                         (const T*)c->A[s], (T*)c->A[1 - s]);
+        kern<<<c->blocks, kThreads, 0, c->stream>>>(a, (const T*)c->P[s], (T*)c->P[1 - s], (const T*)c->A[s],
+                                                    (T*)c->A[1 - s]);
         c->cur = 1 - s;
         c->t += 1;
     }
@@ -660,9 +794,9 @@ template <typename T>
 int mass_typed(mp_ctx* c, int sp, double out[3])
 {
     Args<T> a = make_args<T>(c);
-    const T* P = (const T*)c->P[c->cur] + (size_t)(sp * c->F) * c->geo.N;
+    const T* P = (const T*)c->P[c->cur] + (size_t)sp * c->geo.N * c->FP;
     const size_t NI = (size_t)(c->geo.n_iface > 0 ? c->geo.n_iface : 1);
-    const T* A = (const T*)c->A[c->cur] + (size_t)(sp * c->F) * NI;
+    const T* A = (const T*)c->A[c->cur] + (size_t)sp * NI * c->FP;
     k_mass<T><<<c->blocks, kThreads, 0, c->stream>>>(a, P, A, c->partials);
     std::vector<double> h((size_t)c->blocks * 3);
     MP_CUDA(cudaGetLastError());
@@ -883,19 +1017,20 @@ int mp_get_field(mp_ctx* c, int species, int field, double* free_dense, double* 
     }
     const size_t N = (size_t)c->geo.N;
     const size_t NI = (size_t)(c->geo.n_iface > 0 ? c->geo.n_iface : 1);
-    const size_t fi = (size_t)(species * c->F + field);
-    std::vector<char> buf(N * c->elem), abuf(NI * c->elem);
-    MP_CUDA(cudaMemcpyAsync(buf.data(), (char*)c->P[c->cur] + fi * N * c->elem, N * c->elem, cudaMemcpyDeviceToHost,
-                            c->stream));
-    MP_CUDA(cudaMemcpyAsync(abuf.data(), (char*)c->A[c->cur] + fi * NI * c->elem, NI * c->elem,
+    const size_t FP = (size_t)c->FP, E = c->elem;
+    std::vector<char> buf(N * FP * E), abuf(NI * FP * E);
+    MP_CUDA(cudaMemcpyAsync(buf.data(), (char*)c->P[c->cur] + (size_t)species * N * FP * E, N * FP * E,
+                            cudaMemcpyDeviceToHost, c->stream));
+    MP_CUDA(cudaMemcpyAsync(abuf.data(), (char*)c->A[c->cur] + (size_t)species * NI * FP * E, NI * FP * E,
                             cudaMemcpyDeviceToHost, c->stream));
     MP_CUDA(cudaStreamSynchronize(c->stream));
-    for (size_t n = 0; n < N; ++n)
-        free_dense[n] = c->elem == 8 ? ((double*)buf.data())[n] : (double)((float*)buf.data())[n];
+    auto at = [&](const std::vector<char>& v, size_t i) {
+        return E == 8 ? ((const double*)v.data())[i * FP + field] : (double)((const float*)v.data())[i * FP + field];
+    };
+    for (size_t n = 0; n < N; ++n) free_dense[n] = at(buf, n);
     if (ads_dense) {
         for (size_t n = 0; n < N; ++n) ads_dense[n] = 0.0;
-        for (size_t k = 0; k < c->ilist.size(); ++k)
-            ads_dense[c->ilist[k]] = c->elem == 8 ? ((double*)abuf.data())[k] : (double)((float*)abuf.data())[k];
+        for (size_t k = 0; k < c->ilist.size(); ++k) ads_dense[c->ilist[k]] = at(abuf, k);
     }
     return MP_OK;
 }
@@ -910,31 +1045,26 @@ int mp_set_field(mp_ctx* c, int species, int field, const double* free_dense, co
     }
     const size_t N = (size_t)c->geo.N;
     const size_t NI = (size_t)(c->geo.n_iface > 0 ? c->geo.n_iface : 1);
-    const size_t fi = (size_t)(species * c->F + field);
-    // solid nodes stay zero: read the fluid bits back to mask them
+    const size_t FP = (size_t)c->FP, E = c->elem;
+    // read the species' slab, replace one field, write it back; solid nodes stay zero
     std::vector<uint32_t> fl((size_t)c->geo.W);
+    std::vector<char> buf(N * FP * E), abuf(NI * FP * E);
+    char* dP = (char*)c->P[c->cur] + (size_t)species * N * FP * E;
+    char* dA = (char*)c->A[c->cur] + (size_t)species * NI * FP * E;
     MP_CUDA(cudaMemcpyAsync(fl.data(), c->geo.fluid, fl.size() * 4, cudaMemcpyDeviceToHost, c->stream));
+    MP_CUDA(cudaMemcpyAsync(buf.data(), dP, N * FP * E, cudaMemcpyDeviceToHost, c->stream));
+    MP_CUDA(cudaMemcpyAsync(abuf.data(), dA, NI * FP * E, cudaMemcpyDeviceToHost, c->stream));
     MP_CUDA(cudaStreamSynchronize(c->stream));
-    std::vector<char> buf(N * c->elem), abuf(NI * c->elem, 0);
-    for (size_t n = 0; n < N; ++n) {
-        const bool f = (fl[n >> 5] >> (n & 31)) & 1u;
-        const double v = f ? free_dense[n] : 0.0;
-        if (c->elem == 8)
-            ((double*)buf.data())[n] = v;
+    auto put = [&](std::vector<char>& v, size_t i, double x) {
+        if (E == 8)
+            ((double*)v.data())[i * FP + field] = x;
         else
-            ((float*)buf.data())[n] = (float)v;
-    }
-    for (size_t k = 0; k < c->ilist.size(); ++k) {
-        const double v = ads_dense ? ads_dense[c->ilist[k]] : 0.0;
-        if (c->elem == 8)
-            ((double*)abuf.data())[k] = v;
-        else
-            ((float*)abuf.data())[k] = (float)v;
-    }
-    MP_CUDA(cudaMemcpyAsync((char*)c->P[c->cur] + fi * N * c->elem, buf.data(), N * c->elem, cudaMemcpyHostToDevice,
-                            c->stream));
-    MP_CUDA(cudaMemcpyAsync((char*)c->A[c->cur] + fi * NI * c->elem, abuf.data(), NI * c->elem,
-                            cudaMemcpyHostToDevice, c->stream));
+            ((float*)v.data())[i * FP + field] = (float)x;
+    };
+    for (size_t n = 0; n < N; ++n) put(buf, n, ((fl[n >> 5] >> (n & 31)) & 1u) ? free_dense[n] : 0.0);
+    for (size_t k = 0; k < c->ilist.size(); ++k) put(abuf, k, ads_dense ? ads_dense[c->ilist[k]] : 0.0);
+    MP_CUDA(cudaMemcpyAsync(dP, buf.data(), N * FP * E, cudaMemcpyHostToDevice, c->stream));
+    MP_CUDA(cudaMemcpyAsync(dA, abuf.data(), NI * FP * E, cudaMemcpyHostToDevice, c->stream));
     MP_CUDA(cudaStreamSynchronize(c->stream));
     return MP_OK;
 }
