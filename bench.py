@@ -62,7 +62,11 @@ UNIT = "node-species updates/s"
 
 # DRAM traffic per launch from ncu (dram__bytes_read.sum + dram__bytes_write.sum), valid only
 # while the kernel source hashes to `src_sha`; otherwise reported as null.
-TRAFFIC = {}
+TRAFFIC = {
+    # ncu --set full, python bench.py --profile, k_step<float,2,1> launch 11 (caches flushed
+    # by ncu before the capture, so this is the cold-L2 traffic of one launch)
+    "k_step<float>": {"bytes_per_launch": 48_620_032 + 1_436_160, "src_sha": "1d95494fa159c195"},
+}
 
 
 def _src_sha(name):
@@ -196,6 +200,25 @@ def run_reference(args):
 # ----------------------------------------------------------------------------------------
 # GPU arm
 # ----------------------------------------------------------------------------------------
+def run_profile_case():
+    """The workload's kernels on the same 128^3 medium, briefly, for ncu --set full
+    captures (python bench.py --profile): LB launches 1-30, k_init, MP launches 1-20."""
+    import torch
+    from paper_1303_2470_gb300 import build
+    build.build()
+    from paper_1303_2470_gb300 import mp
+    solid, _ = make_medium()
+    sd = torch.as_tensor(solid).cuda()
+    u = torch.zeros((3,) + solid.shape, dtype=torch.float32, device="cuda")
+    mp.lb_steady(sd, (1.83e-3, 0, 0), u, tau=WORKLOAD["tau"], tol=0.0, max_steps=30, check_every=30)
+    ctx = mp.mp_init(sd, u, WORKLOAD["D_b"], WORKLOAD["k_a"], WORKLOAD["k_d"], allow_negative=True, capacity=64)
+    mp.mp_step(ctx, 20)
+    torch.cuda.synchronize()
+    print(json.dumps({"profile_case": "ok", "n_fluid": mp.mp_info(ctx)["n_fluid"]}))
+    ctx.close()
+    return 0
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -204,10 +227,15 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--mp-steps", type=int, default=WORKLOAD["mp_steps"])
+    ap.add_argument("--profile", action="store_true",
+                    help="short run of the same medium and kernels for ncu captures: 30 LB steps, "
+                         "mp_init and 20 MP steps, no timing")
     args = ap.parse_args()
     WORKLOAD["mp_steps"] = args.mp_steps
     if args.impl == "reference":
         return run_reference(args)
+    if args.profile:
+        return run_profile_case()
 
     import torch
     import torch.distributed as dist

@@ -243,13 +243,15 @@ __device__ __forceinline__ void block_sum_store(const T (&v)[kMax], int cnt, dou
 }
 
 // Last block of the grid: FP64 sum of the per-block partials of each of the K series
-// values, in a fixed order; `emit(k, total)` is called by thread 0.
+// values, in a fixed order; `emit(k, total)` is called by thread 0. Thread j < K must have
+// written partial j of this block (callers write them with threads 0..K-1).
 template <typename Emit>
 __device__ __forceinline__ bool grid_total(double* partials, int K, unsigned int* ticket, Emit emit)
 {
     __shared__ unsigned int s_last;
     __shared__ double s_red[kWarps];
-    __threadfence();
+    // the threads that wrote this block's partials make them visible before the ticket
+    if (threadIdx.x < K) __threadfence();
     __syncthreads();
     if (threadIdx.x == 0) s_last = (atomicAdd(ticket, 1u) == gridDim.x - 1) ? 1u : 0u;
     __syncthreads();
