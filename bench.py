@@ -132,6 +132,17 @@ class ClockSampler:
                 "reasons": reasons, "samples": len(rows)}
 
 
+def aggregate(seconds, units_per_rank, world, dist=None, device=None):
+    """Whole-job throughput of N replicas: the slowest rank's time (max over ranks) and all
+    ranks' units over it. With world == 1 no collective is used."""
+    import torch
+    t = torch.tensor([float(seconds)], dtype=torch.float64, device=device)
+    if world > 1:
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    slowest = float(t.item())
+    return slowest, units_per_rank * world / slowest
+
+
 def make_medium():
     from paper_1303_2470_gb300 import media
     nz, ny, nx = WORKLOAD["lattice"][::-1]
@@ -316,12 +327,9 @@ def main():
     if world > 1:
         dist.barrier()
     clk = clocks.stop()
-    t = torch.tensor([total_ms], dtype=torch.float64, device=dev)
-    if world > 1:
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-    total_ms_max = float(t.item())
     units_per_job = n_fluid * WORKLOAD["species"] * WORKLOAD["mp_steps"]
-    value = units_per_job * args.steps * world / (total_ms_max / 1e3)
+    slowest_s, value = aggregate(total_ms / 1e3, units_per_job * args.steps, world, dist, dev)
+    total_ms_max = slowest_s * 1e3
 
     # end to end through the public API: host solid mask in, host Z(t)/D(t) out
     Zh = torch.empty(WORKLOAD["mp_steps"] + 2, dtype=torch.float64, pin_memory=True).numpy()
@@ -335,10 +343,7 @@ def main():
         torch.cuda.synchronize()
         e2e_s += time.perf_counter() - t0
         ctx.close()
-    et = torch.tensor([e2e_s], dtype=torch.float64, device=dev)
-    if world > 1:
-        dist.all_reduce(et, op=dist.ReduceOp.MAX)
-    e2e_value = units_per_job * args.steps * world / float(et.item())
+    _, e2e_value = aggregate(e2e_s, units_per_job * args.steps, world, dist, dev)
 
     # roofline of the dominant kernel, from the live event timings above
     peak, peak_kind = _peaks()
