@@ -211,6 +211,81 @@ def run_reference(args):
 # ----------------------------------------------------------------------------------------
 # GPU arm
 # ----------------------------------------------------------------------------------------
+BATCHED = {
+    "workload": "three random-sphere media 64^3, 128^3, 192^3 (porosity U[0.35,0.5], radius "
+                "U{4..8}, seeds 2-4), 16 species each (D_b U[0.01,0.1], k_a, k_d logU[1e-4,1e-1])",
+    "sizes": [64, 128, 192],
+    "seeds": [2, 3, 4],
+    "species": 16,
+    "mean_u": 0.01,
+}
+
+
+def run_batched(args):
+    """Config of batched species and uneven media: every medium gets its LB flow, then all
+    48 species advance (a) in one grouped launch per step (CUDA graph, autotuned block) and
+    (b) one species per launch; both are timed over the same number of steps. The fields
+    of (a) and (b) are identical (tests/test_gpu_group.py), so the accuracy is equal."""
+    import torch
+    from paper_1303_2470_gb300 import build, media
+    build.build()
+    from paper_1303_2470_gb300 import mp
+    rng = np.random.default_rng(2024)
+    steps = max(args.mp_steps // 20, 200) if args.mp_steps else 500
+    meds = []
+    for n, seed in zip(BATCHED["sizes"], BATCHED["seeds"]):
+        phi = float(rng.uniform(0.35, 0.5))
+        solid, _ = media.random_spheres((n, n, n), [4, 5, 6, 7, 8], phi, seed)
+        sd = torch.as_tensor(solid).cuda()
+        u = torch.zeros((3,) + solid.shape, dtype=torch.float32, device="cuda")
+        mp.lb_steady(sd, (1e-5, 0, 0), u, tol=1e-7, max_steps=100_000, check_every=100)
+        fl = sd == 0
+        F = 1e-5 * BATCHED["mean_u"] / float(u[0][fl].double().mean())
+        lb_steps, _, _ = mp.lb_steady(sd, (F, 0, 0), u, tol=1e-7, max_steps=100_000, check_every=100)
+        Db, ka, kd = media.species(BATCHED["species"], seed=seed + 100)
+        meds.append((sd, u, Db, ka, kd, int(fl.sum()), phi, lb_steps))
+    units = sum(m[5] for m in meds) * BATCHED["species"] * steps
+    cap = 2 * steps + 40
+
+    def timed(fn):
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        fn()
+        e1.record()
+        torch.cuda.synchronize()
+        return e0.elapsed_time(e1) / 1e3
+
+    ctxs = [mp.mp_init_batch(sd, u, Db, ka, kd, capacity=cap, allow_negative=True)
+            for sd, u, Db, ka, kd, *_ in meds]
+    g = mp.mp_group_create(ctxs, graph_steps=64, autotune=True)
+    mp.mp_group_step(g, 10)
+    t_group = timed(lambda: mp.mp_group_step(g, steps))
+    block = mp.mp_group_block_size(g)
+    g.close()
+    for c in ctxs:
+        c.close()
+    singles = [mp.mp_init(sd, u, Db[s], ka[s], kd[s], capacity=cap, allow_negative=True)
+               for sd, u, Db, ka, kd, *_ in meds for s in range(BATCHED["species"])]
+    for c in singles:
+        mp.mp_step(c, 10)
+
+    def one_by_one():
+        for _ in range(steps):
+            for c in singles:
+                mp.mp_step(c, 1)
+    t_single = timed(one_by_one)
+    for c in singles:
+        c.close()
+    line = {"metric": "batched sorption-MP node-species updates/s", "workload": BATCHED["workload"],
+            "steps": steps, "grouped": units / t_group, "one_species_per_launch": units / t_single,
+            "speedup": t_single / t_group, "block": block, "graph_steps": 64,
+            "media": [{"n": int(m[0].shape[0]), "porosity": m[6], "n_fluid": m[5], "lb_steps": m[7]} for m in meds],
+            "unit": UNIT}
+    print(json.dumps(line))
+    return 0
+
+
 def run_profile_case():
     """The workload's kernels on the same 128^3 medium, briefly, for ncu --set full
     captures (python bench.py --profile): LB launches 1-30, k_init, MP launches 1-20."""
@@ -238,6 +313,9 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--mp-steps", type=int, default=WORKLOAD["mp_steps"])
+    ap.add_argument("--workload", default="porous128", choices=["porous128", "batched"],
+                    help="porous128: the single-species 128^3 job (the bench line); batched: three "
+                         "media x 16 species, grouped launch vs one species per launch")
     ap.add_argument("--profile", action="store_true",
                     help="short run of the same medium and kernels for ncu captures: 30 LB steps, "
                          "mp_init and 20 MP steps, no timing")
@@ -247,6 +325,8 @@ def main():
         return run_reference(args)
     if args.profile:
         return run_profile_case()
+    if args.workload == "batched":
+        return run_batched(args)
 
     import torch
     import torch.distributed as dist

@@ -167,6 +167,36 @@ int mp_set_field(mp_ctx* c, int species, int field, const double* free_dense,
                  const double* ads_dense);
 
 /*
+ * Groups -- several contexts (media of any sizes, each with its own species) advanced
+ * together, one kernel launch per step for all of them.
+ *
+ * Paper: the same step as mp_step (Sec. "Algorithm"); the paper treats one species in one
+ * medium at a time, and a group only batches independent problems.
+ *
+ * mp_group_create
+ *  out          receives the group handle.
+ *  ctxs, n      1..16 distinct FP32 contexts with the same field layout (the same number of
+ *               velocity moments, padded: 1 or 2-3). They keep their own streams, series
+ *               and fields; while grouped, mp_step on them fails (use mp_group_step), and
+ *               the group must be freed before any of them.
+ *  graph_steps  even number of steps captured once into a CUDA graph and replayed for long
+ *               runs (0 = plain launches). The group runs on its own internal stream,
+ *               ordered after and before the contexts' streams with events.
+ *  autotune     nonzero: time 20 steps at block sizes 128, 256 and 512 on a copy of the
+ *               current state (restored afterwards) and keep the fastest; otherwise 256.
+ *               Needs at least one free entry in every context's series.
+ * mp_group_step advances every context n steps (same results as separate mp_step calls:
+ * identical fields; Z and D equal up to the order of the FP64 block sums when the block
+ * size differs from 256). mp_group_block_size returns the block size in use.
+ * Errors: MP_EINVAL, MP_ENOMEM, MP_ECUDA.
+ */
+typedef struct mp_group mp_group;
+int mp_group_create(mp_group** out, mp_ctx* const* ctxs, int n, int graph_steps, int autotune);
+int mp_group_step(mp_group* g, int64_t n);
+int mp_group_block_size(mp_group* g);
+void mp_group_free(mp_group* g);
+
+/*
  * mp_classify -- node classes of a medium, as used by every other entry point.
  *
  * Paper: Sec. "Algorithm", the three node classes of the Boltzmann weights: solid S, fluid F

@@ -18,6 +18,8 @@
 // packed in one 16-byte vector, so that a neighbour's link probability costs one load and
 // three fused multiply-adds. All species sharing the medium reuse the flow-dependent part
 // q_i of p_i = w_i (q_i + lambda/2); only lambda/2, p_a and p_d differ per species.
+#include <algorithm>
+#include <climits>
 #include <cmath>
 #include <cstdio>
 #include <cstring>
@@ -242,31 +244,31 @@ __device__ __forceinline__ void block_sum_store(const T (&v)[kMax], int cnt, dou
     __syncthreads();
 }
 
-// Last block of the grid: FP64 sum of the per-block partials of each of the K series
-// values, in a fixed order; `emit(k, total)` is called by thread 0. Thread j < K must have
-// written partial j of this block (callers write them with threads 0..K-1).
-template <typename Emit>
-__device__ __forceinline__ bool grid_total(double* partials, int K, unsigned int* ticket, Emit emit)
+// Last block of a launch (or of one context's block range in a grouped launch): FP64 sum of
+// the per-block partials of each of the K series values, in a fixed order; `emit(k, total)`
+// is called by thread 0. Thread j < K must have written partial j of this block.
+template <int kB, typename Emit>
+__device__ __forceinline__ bool grid_total(double* partials, int K, unsigned int* ticket, int nblk, Emit emit)
 {
     __shared__ unsigned int s_last;
-    __shared__ double s_red[kWarps];
+    __shared__ double s_red[kB / 32];
     // the threads that wrote this block's partials make them visible before the ticket
     if (threadIdx.x < K) __threadfence();
     __syncthreads();
-    if (threadIdx.x == 0) s_last = (atomicAdd(ticket, 1u) == gridDim.x - 1) ? 1u : 0u;
+    if (threadIdx.x == 0) s_last = (atomicAdd(ticket, 1u) == (unsigned)nblk - 1) ? 1u : 0u;
     __syncthreads();
     if (!s_last) return false;
     __threadfence();
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     for (int k = 0; k < K; ++k) {
         double v = 0.0;
-        for (int b = threadIdx.x; b < (int)gridDim.x; b += kThreads) v += __ldcg(partials + (size_t)b * K + k);
+        for (int b = threadIdx.x; b < nblk; b += kB) v += __ldcg(partials + (size_t)b * K + k);
         v = warp_sum(v);
         if (lane == 0) s_red[warp] = v;
         __syncthreads();
         if (threadIdx.x == 0) {
             double tot = 0.0;
-            for (int w = 0; w < kWarps; ++w) tot += s_red[w];
+            for (int w = 0; w < kB / 32; ++w) tot += s_red[w];
             emit(k, tot);
         }
         __syncthreads();
@@ -294,19 +296,19 @@ __device__ __forceinline__ bool grid_total(double* partials, int K, unsigned int
 // and reused by every species. Each warp reduces its Z terms with shuffles into shared
 // memory; the block combines them after one barrier.
 // ---------------------------------------------------------------------------------------
-template <typename T, int FP, bool kSingle>
-__global__ void __launch_bounds__(kThreads)
-    k_step(const Args<T> a, const T* __restrict__ P, T* __restrict__ Pn, const T* __restrict__ A,
-           T* __restrict__ An)
+template <typename T, int FP, bool kSingle, int kB>
+__device__ __forceinline__ void step_body(const Args<T>& a, int blk, int nblk, const T* __restrict__ P,
+                                          T* __restrict__ Pn, const T* __restrict__ A, T* __restrict__ An)
 {
+    constexpr int kW = kB / 32;
     using V = FieldVec<T, FP>;
     const V* __restrict__ Pv = reinterpret_cast<const V*>(P);
     V* __restrict__ Pnv = reinterpret_cast<V*>(Pn);
     const V* __restrict__ Av = reinterpret_cast<const V*>(A);
     V* __restrict__ Anv = reinterpret_cast<V*>(An);
-    __shared__ double s_part[kWarps][MP_MAX_SPECIES * (kMaxF - 1)];
+    __shared__ double s_part[kW][MP_MAX_SPECIES * (kMaxF - 1)];
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    const int k = blockIdx.x * kThreads + threadIdx.x;
+    const int k = blk * kB + threadIdx.x;
     const bool active = k < a.NF;
     const int K = a.S * a.M;
 
@@ -426,10 +428,10 @@ __global__ void __launch_bounds__(kThreads)
         }
     }
     __syncthreads();
-    for (int j = threadIdx.x; j < K; j += kThreads) {
+    for (int j = threadIdx.x; j < K; j += kB) {
         double t = 0.0;
-        for (int w = 0; w < kWarps; ++w) t += s_part[w][j];
-        a.partials[(size_t)blockIdx.x * K + j] = t;
+        for (int w = 0; w < kW; ++w) t += s_part[w][j];
+        a.partials[(size_t)blk * K + j] = t;
     }
     const long long cap = a.cap;
     double* Z = a.Z;
@@ -438,12 +440,61 @@ __global__ void __launch_bounds__(kThreads)
     __shared__ long long s_t1;
     if (threadIdx.x == 0) s_t1 = *((volatile long long*)tdev) + 1;
     // s_t1 is only read by thread 0 of the last block, after the barriers in grid_total
-    bool last = grid_total(a.partials, K, a.ticket, [&](int kk, double tot) {
+    bool last = grid_total<kB>(a.partials, K, a.ticket, nblk, [&](int kk, double tot) {
         const long long t1 = s_t1;
         Z[(size_t)kk * cap + t1] = tot;
         D[(size_t)kk * cap + t1] = D[(size_t)kk * cap + t1 - 1] + tot;
     });
     if (last && threadIdx.x == 0) *tdev = s_t1;
+}
+
+template <typename T, int FP, bool kSingle>
+__global__ void __launch_bounds__(kThreads)
+    k_step(const Args<T> a, const T* __restrict__ P, T* __restrict__ Pn, const T* __restrict__ A,
+           T* __restrict__ An)
+{
+    step_body<T, FP, kSingle, kThreads>(a, blockIdx.x, gridDim.x, P, Pn, A, An);
+}
+
+// ---------------------------------------------------------------------------------------
+// Grouped step: one launch advances several contexts (media of different sizes, each with
+// its own species). Blocks [bofs[c], bofs[c+1]) work on context c; each context keeps its
+// own partials, ticket and series, so the result equals separate launches with the same
+// block size. The per-context arguments and the two phases' field pointers live in device
+// memory owned by the group.
+// ---------------------------------------------------------------------------------------
+constexpr int kMaxGroup = 16;
+
+struct GroupPtrs {
+    const float* P;
+    float* Pn;
+    const float* A;
+    float* An;
+};
+
+struct GroupArgs {
+    const Args<float>* args;    // [n]
+    const GroupPtrs* ptrs;      // [2][n]: field pointers of step phase 0 and 1
+    int bofs[kMaxGroup + 1];    // block prefix
+    int n;
+};
+
+template <int FP, bool kSingle, int kB>
+__global__ void __launch_bounds__(kB) k_step_group(const GroupArgs g, int phase)
+{
+    // context of this block; constant indices only, so the parameter array stays in the
+    // constant bank
+    int c = 0, b0 = 0, b1 = g.bofs[1];
+#pragma unroll
+    for (int j = 1; j < kMaxGroup; ++j) {
+        if (j < g.n && (int)blockIdx.x >= g.bofs[j]) {
+            c = j;
+            b0 = g.bofs[j];
+            b1 = g.bofs[j + 1];
+        }
+    }
+    const GroupPtrs p = g.ptrs[phase * g.n + c];
+    step_body<float, FP, kSingle, kB>(g.args[c], (int)blockIdx.x - b0, b1 - b0, p.P, p.Pn, p.A, p.An);
 }
 
 // ---------------------------------------------------------------------------------------
@@ -508,7 +559,7 @@ __global__ void __launch_bounds__(kThreads)
     const long long cap = a.cap;
     double* Z = a.Z;
     double* D = a.D;
-    bool last = grid_total(a.partials, K2, a.ticket, [&](int kk, double tot) {
+    bool last = grid_total<kThreads>(a.partials, K2, a.ticket, (int)gridDim.x, [&](int kk, double tot) {
         const int series = kk / 2;
         if ((kk & 1) == 0) {
             Z[(size_t)series * cap + 0] = tot;
@@ -645,6 +696,7 @@ struct mp_ctx {
     std::vector<int32_t> ilist;
     size_t elem = 4;
     int FP = 2;  // fields per node in the [species][node][field] layout (F padded to 2 or 4)
+    mp_group* owner = nullptr;  // set while the context steps as part of a group
 };
 
 namespace {
@@ -731,7 +783,8 @@ int init_typed(mp_ctx* c, const float* u_in, int init_density)
     MP_CUDA(cudaMemsetAsync(c->tdev, 0, sizeof(long long), c->stream));
     // per-block partials: 2 S M values (initialisation) or 3 (mass check), whichever is more
     const size_t per_block = (size_t)(2 * Kser > 3 ? 2 * Kser : 3);
-    MP_CUDA(cudaMalloc(&c->partials, sizeof(double) * (size_t)c->blocks * per_block));
+    const size_t max_blocks = (size_t)((c->geo.n_fluid + 127) / 128);  // smallest group block size
+    MP_CUDA(cudaMalloc(&c->partials, sizeof(double) * (max_blocks > (size_t)c->blocks ? max_blocks : c->blocks) * per_block));
     MP_CUDA(cudaMalloc(&c->ticket, sizeof(unsigned int)));
     MP_CUDA(cudaMemsetAsync(c->ticket, 0, sizeof(unsigned int), c->stream));
     k_pack_flow<T><<<(N + 255) / 256, 256, 0, c->stream>>>(u_in, c->geo.fluid, N, (Flow4<T>*)c->u4);
@@ -955,6 +1008,10 @@ int mp_step(mp_ctx* c, int64_t n)
         set_error("the Z/D series is full: capacity " + std::to_string(c->cap) + " time points");
         return MP_EINVAL;
     }
+    if (c->owner) {
+        set_error("the context belongs to a group: step it with mp_group_step");
+        return MP_EINVAL;
+    }
     return c->precision == MP_FP64 ? step_typed<double>(c, n) : step_typed<float>(c, n);
 }
 
@@ -1077,5 +1134,310 @@ void mp_free(mp_ctx* c)
     if (c->stream) cudaStreamSynchronize(c->stream);
     destroy(c);
 }
+
+}  // extern "C"
+
+// ---------------------------------------------------------------------------------------
+// Groups: several FP32 contexts advanced by one launch per step (k_step_group), with an
+// autotuned block size and CUDA-graph replay of runs of steps.
+// ---------------------------------------------------------------------------------------
+struct mp_group {
+    std::vector<mp_ctx*> ctx;
+    int FP = 2;
+    bool single = true;
+    int block = kThreads;
+    cudaStream_t stream = nullptr;
+    cudaEvent_t ev = nullptr;
+    Args<float>* d_args = nullptr;
+    GroupPtrs* d_ptrs = nullptr;
+    GroupArgs ga;
+    int phase = 0;
+    cudaGraph_t graph = nullptr;
+    cudaGraphExec_t exec = nullptr;
+    int graph_steps = 0;
+};
+
+namespace {
+
+void group_set_block(mp_group* g, int block)
+{
+    g->block = block;
+    g->ga.bofs[0] = 0;
+    for (size_t c = 0; c < g->ctx.size(); ++c)
+        g->ga.bofs[c + 1] = g->ga.bofs[c] + (int)((g->ctx[c]->geo.n_fluid + block - 1) / block);
+}
+
+template <int FP, bool kSingle>
+void launch_group_fp(mp_group* g)
+{
+    const int blocks = g->ga.bofs[g->ctx.size()];
+    if (g->block == 128)
+        k_step_group<FP, kSingle, 128><<<blocks, 128, 0, g->stream>>>(g->ga, g->phase);
+    else if (g->block == 512)
+        k_step_group<FP, kSingle, 512><<<blocks, 512, 0, g->stream>>>(g->ga, g->phase);
+    else
+        k_step_group<FP, kSingle, 256><<<blocks, 256, 0, g->stream>>>(g->ga, g->phase);
+}
+
+// one grouped step: launch, then advance every context's phase, buffer and time
+void group_launch(mp_group* g, bool advance_ctx)
+{
+    if (g->FP == 2)
+        g->single ? launch_group_fp<2, true>(g) : launch_group_fp<2, false>(g);
+    else
+        g->single ? launch_group_fp<4, true>(g) : launch_group_fp<4, false>(g);
+    g->phase ^= 1;
+    if (advance_ctx)
+        for (mp_ctx* c : g->ctx) {
+            c->cur ^= 1;
+            c->t += 1;
+        }
+}
+
+int group_sync_in(mp_group* g)
+{
+    for (mp_ctx* c : g->ctx) {
+        MP_CUDA(cudaEventRecord(g->ev, c->stream));
+        MP_CUDA(cudaStreamWaitEvent(g->stream, g->ev, 0));
+    }
+    return MP_OK;
+}
+
+int group_sync_out(mp_group* g)
+{
+    MP_CUDA(cudaEventRecord(g->ev, g->stream));
+    for (mp_ctx* c : g->ctx) MP_CUDA(cudaStreamWaitEvent(c->stream, g->ev, 0));
+    return MP_OK;
+}
+
+// Time `steps` grouped steps at each candidate block size on the current state, restoring
+// fields, adsorbed arrays, buffers, times and series counters after each trial.
+int group_autotune(mp_group* g, int steps)
+{
+    const int cand[3] = {128, 256, 512};
+    std::vector<void*> bP(g->ctx.size(), nullptr), bA(g->ctx.size(), nullptr);
+    std::vector<size_t> nP(g->ctx.size()), nA(g->ctx.size());
+    int rc = MP_OK;
+    for (size_t c = 0; c < g->ctx.size() && rc == MP_OK; ++c) {
+        mp_ctx* x = g->ctx[c];
+        const size_t NI = (size_t)(x->geo.n_iface > 0 ? x->geo.n_iface : 1);
+        nP[c] = (size_t)x->S * x->geo.N * x->FP * sizeof(float);
+        nA[c] = (size_t)x->S * NI * x->FP * sizeof(float);
+        if (cudaMalloc(&bP[c], nP[c]) != cudaSuccess || cudaMalloc(&bA[c], nA[c]) != cudaSuccess) {
+            (void)cudaGetLastError();
+            set_error("autotune: no device memory for the state backup");
+            rc = MP_ENOMEM;
+        }
+    }
+    std::vector<int> cur0(g->ctx.size());
+    std::vector<long long> t0(g->ctx.size());
+    for (size_t c = 0; c < g->ctx.size(); ++c) {
+        cur0[c] = g->ctx[c]->cur;
+        t0[c] = g->ctx[c]->t;
+    }
+    const int phase0 = g->phase;
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    if (rc == MP_OK && (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess)) {
+        set_error("autotune: event creation failed");
+        rc = MP_ECUDA;
+    }
+    float best_ms = 1e30f;
+    int best = g->block;
+    for (int k = 0; k < 3 && rc == MP_OK; ++k) {
+        cudaError_t e = cudaSuccess;
+        for (size_t c = 0; c < g->ctx.size() && e == cudaSuccess; ++c) {
+            mp_ctx* x = g->ctx[c];
+            e = cudaMemcpyAsync(bP[c], x->P[x->cur], nP[c], cudaMemcpyDeviceToDevice, g->stream);
+            if (e == cudaSuccess) e = cudaMemcpyAsync(bA[c], x->A[x->cur], nA[c], cudaMemcpyDeviceToDevice, g->stream);
+        }
+        group_set_block(g, cand[k]);
+        group_launch(g, false);  // warm-up launch of this configuration
+        if (e == cudaSuccess) e = cudaEventRecord(e0, g->stream);
+        for (int s2 = 0; s2 < steps; ++s2) group_launch(g, false);
+        if (e == cudaSuccess) e = cudaEventRecord(e1, g->stream);
+        if (e == cudaSuccess) e = cudaEventSynchronize(e1);
+        float ms = 0.f;
+        if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, e0, e1);
+        if (e == cudaSuccess) e = cudaGetLastError();
+        // restore the state the trial started from
+        g->phase = phase0;
+        for (size_t c = 0; c < g->ctx.size() && e == cudaSuccess; ++c) {
+            mp_ctx* x = g->ctx[c];
+            e = cudaMemcpyAsync(x->P[cur0[c]], bP[c], nP[c], cudaMemcpyDeviceToDevice, g->stream);
+            if (e == cudaSuccess) e = cudaMemcpyAsync(x->A[cur0[c]], bA[c], nA[c], cudaMemcpyDeviceToDevice, g->stream);
+            if (e == cudaSuccess)
+                e = cudaMemcpyAsync(x->tdev, &t0[c], sizeof(long long), cudaMemcpyHostToDevice, g->stream);
+            if (e == cudaSuccess) e = cudaStreamSynchronize(g->stream);
+        }
+        if (e != cudaSuccess) {
+            rc = cuda_fail(e, "autotune");
+            break;
+        }
+        if (ms < best_ms) {
+            best_ms = ms;
+            best = cand[k];
+        }
+    }
+    if (e0) cudaEventDestroy(e0);
+    if (e1) cudaEventDestroy(e1);
+    for (size_t c = 0; c < g->ctx.size(); ++c) {
+        cudaFree(bP[c]);
+        cudaFree(bA[c]);
+    }
+    group_set_block(g, best);
+    return rc;
+}
+
+void group_destroy(mp_group* g)
+{
+    if (!g) return;
+    if (g->stream) cudaStreamSynchronize(g->stream);
+    for (mp_ctx* c : g->ctx) c->owner = nullptr;
+    if (g->exec) cudaGraphExecDestroy(g->exec);
+    if (g->graph) cudaGraphDestroy(g->graph);
+    cudaFree(g->d_args);
+    cudaFree(g->d_ptrs);
+    if (g->ev) cudaEventDestroy(g->ev);
+    if (g->stream) cudaStreamDestroy(g->stream);
+    delete g;
+}
+
+}  // namespace
+
+extern "C" {
+
+int mp_group_create(mp_group** out, mp_ctx* const* ctxs, int n, int graph_steps, int autotune)
+{
+    clear_error();
+    if (!out || !ctxs || n < 1 || n > kMaxGroup || graph_steps < 0 || graph_steps % 2) {
+        set_error("mp_group_create: need 1..16 contexts and an even graph_steps >= 0");
+        return MP_EINVAL;
+    }
+    for (int c = 0; c < n; ++c) {
+        if (!ctxs[c] || ctxs[c]->precision != MP_FP32 || ctxs[c]->owner || ctxs[c]->FP != ctxs[0]->FP) {
+            set_error("mp_group_create: contexts must be distinct, FP32, ungrouped, with the same field layout");
+            return MP_EINVAL;
+        }
+        for (int d = 0; d < c; ++d)
+            if (ctxs[d] == ctxs[c]) {
+                set_error("mp_group_create: a context is listed twice");
+                return MP_EINVAL;
+            }
+    }
+    mp_group* g = new (std::nothrow) mp_group();
+    if (!g) {
+        set_error("host allocation failed");
+        return MP_ENOMEM;
+    }
+    g->ctx.assign(ctxs, ctxs + n);
+    g->FP = ctxs[0]->FP;
+    g->single = true;
+    for (mp_ctx* c : g->ctx) g->single = g->single && c->S == 1;
+    g->ga.n = n;
+    int rc = MP_OK;
+    cudaError_t e = cudaStreamCreateWithFlags(&g->stream, cudaStreamNonBlocking);
+    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&g->ev, cudaEventDisableTiming);
+    if (e == cudaSuccess) e = cudaMalloc(&g->d_args, sizeof(Args<float>) * n);
+    if (e == cudaSuccess) e = cudaMalloc(&g->d_ptrs, sizeof(GroupPtrs) * 2 * n);
+    if (e == cudaSuccess) {
+        std::vector<Args<float>> h_args(n);
+        std::vector<GroupPtrs> h_ptrs(2 * n);
+        for (int c = 0; c < n; ++c) {
+            mp_ctx* x = g->ctx[c];
+            h_args[c] = make_args<float>(x);
+            for (int ph = 0; ph < 2; ++ph) {
+                const int in = (x->cur + ph) & 1;
+                h_ptrs[ph * n + c] = GroupPtrs{(const float*)x->P[in], (float*)x->P[1 - in], (const float*)x->A[in],
+                                               (float*)x->A[1 - in]};
+            }
+        }
+        e = cudaMemcpy(g->d_args, h_args.data(), sizeof(Args<float>) * n, cudaMemcpyHostToDevice);
+        if (e == cudaSuccess) e = cudaMemcpy(g->d_ptrs, h_ptrs.data(), sizeof(GroupPtrs) * 2 * n, cudaMemcpyHostToDevice);
+    }
+    if (e != cudaSuccess) {
+        rc = cuda_fail(e, "mp_group_create");
+        group_destroy(g);
+        return rc;
+    }
+    g->ga.args = g->d_args;
+    g->ga.ptrs = g->d_ptrs;
+    group_set_block(g, kThreads);
+    for (mp_ctx* c : g->ctx) c->owner = g;
+    if (autotune) {
+        long long room = LLONG_MAX;
+        for (mp_ctx* c : g->ctx) room = std::min(room, c->cap - 1 - c->t);
+        if (room < 1) {
+            set_error("mp_group_create: autotune needs free room in every Z/D series");
+            group_destroy(g);
+            return MP_EINVAL;
+        }
+        rc = group_sync_in(g);
+        if (rc == MP_OK) rc = group_autotune(g, 20);
+        if (rc != MP_OK) {
+            group_destroy(g);
+            return rc;
+        }
+    }
+    if (graph_steps > 0) {
+        // graph_steps launches alternating the two phases, starting at phase 0
+        const int phase0 = g->phase;
+        g->phase = 0;
+        e = cudaStreamBeginCapture(g->stream, cudaStreamCaptureModeThreadLocal);
+        if (e == cudaSuccess) {
+            for (int k = 0; k < graph_steps; ++k) group_launch(g, false);
+            e = cudaStreamEndCapture(g->stream, &g->graph);
+        }
+        if (e == cudaSuccess) e = cudaGraphInstantiate(&g->exec, g->graph, 0);
+        g->phase = phase0;
+        if (e != cudaSuccess) {
+            rc = cuda_fail(e, "mp_group_create: graph capture");
+            group_destroy(g);
+            return rc;
+        }
+        g->graph_steps = graph_steps;
+    }
+    *out = g;
+    return MP_OK;
+}
+
+int mp_group_step(mp_group* g, int64_t n)
+{
+    clear_error();
+    if (!g || n < 0) {
+        set_error("mp_group_step: group is NULL or n < 0");
+        return MP_EINVAL;
+    }
+    for (mp_ctx* c : g->ctx)
+        if (c->t + n > c->cap - 1) {
+            set_error("mp_group_step: a context's Z/D series is full");
+            return MP_EINVAL;
+        }
+    if (int rc = group_sync_in(g)) return rc;
+    while (n > 0 && g->graph_steps > 0 && g->phase != 0) {
+        group_launch(g, true);
+        --n;
+    }
+    while (g->graph_steps > 0 && n >= g->graph_steps) {
+        MP_CUDA(cudaGraphLaunch(g->exec, g->stream));
+        for (mp_ctx* c : g->ctx) {
+            c->cur = (c->cur + g->graph_steps) & 1;
+            c->t += g->graph_steps;
+        }
+        n -= g->graph_steps;
+    }
+    while (n > 0) {
+        group_launch(g, true);
+        --n;
+    }
+    MP_CUDA(cudaGetLastError());
+    return group_sync_out(g);
+}
+
+int mp_group_block_size(mp_group* g)
+{
+    return g ? g->block : 0;
+}
+
+void mp_group_free(mp_group* g) { group_destroy(g); }
 
 }  // extern "C"

@@ -75,8 +75,14 @@ _lib.mp_classify.argtypes = [ctypes.POINTER(mp_geometry), _c_vp, ctypes.POINTER(
                              ctypes.POINTER(_c_i64), ctypes.POINTER(_c_i64), _c_vp]
 _lib.mp_step_noalloc.argtypes = [_c_int, _c_int, _c_int, _c_vp, _c_vp, _c_dbl, _c_dbl, _c_dbl, _c_int,
                                  _c_vp, _c_vp, _c_vp, _c_vp, _c_vp, _c_vp]
+_lib.mp_group_create.argtypes = [ctypes.POINTER(_c_vp), ctypes.POINTER(_c_vp), _c_int, _c_int, _c_int]
+_lib.mp_group_step.argtypes = [_c_vp, _c_i64]
+_lib.mp_group_block_size.argtypes = [_c_vp]
+_lib.mp_group_free.argtypes = [_c_vp]
+_lib.mp_group_free.restype = None
 for _f in ("mp_init", "mp_init_batch", "mp_step", "mp_vacf", "mp_mass", "mp_info", "mp_get_field",
-           "mp_set_field", "lb_steady", "mp_classify", "mp_step_noalloc"):
+           "mp_set_field", "lb_steady", "mp_classify", "mp_step_noalloc", "mp_group_create",
+           "mp_group_step", "mp_group_block_size"):
     getattr(_lib, _f).restype = _c_int
 
 
@@ -260,6 +266,45 @@ def mp_step_noalloc(solid, u, D_b, k_a, k_d, direction, X, X_ads, X_out, X_ads_o
     _check(_lib.mp_step_noalloc(nx, ny, nz, _addr(solid), _addr(u), float(D_b), float(k_a), float(k_d),
                                 int(direction), _addr(X), _addr(X_ads), _addr(X_out), _addr(X_ads_out),
                                 _addr(Z_out), _stream(stream)))
+
+
+class Group:
+    """Owning handle of an mp_group*; keeps its contexts alive and frees first."""
+
+    def __init__(self, ptr, ctxs):
+        self.ptr = ptr
+        self.ctxs = list(ctxs)
+
+    def close(self):
+        if self.ptr:
+            _lib.mp_group_free(self.ptr)
+            self.ptr = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def mp_group_create(ctxs, graph_steps: int = 0, autotune: bool = False) -> Group:
+    """mp_group_create of include/mp.h over a list of Context objects."""
+    arr = (_c_vp * len(ctxs))(*[c.ptr for c in ctxs])
+    out = _c_vp()
+    _check(_lib.mp_group_create(ctypes.byref(out), arr, len(ctxs), int(graph_steps), int(bool(autotune))))
+    return Group(out, ctxs)
+
+
+def mp_group_step(group: Group, n: int):
+    _check(_lib.mp_group_step(group.ptr, int(n)))
+
+
+def mp_group_block_size(group: Group) -> int:
+    return int(_lib.mp_group_block_size(group.ptr))
+
+
+def mp_group_free(group: Group):
+    group.close()
 
 
 def mp_free(ctx: Context):
