@@ -286,6 +286,29 @@ def run_batched(args):
     return 0
 
 
+def run_profile_batched():
+    """Two random-sphere media (96^3, 128^3) x 16 species, 30 LB steps each, then 8 grouped
+    steps without graph or autotune: `k_step_group` launches for ncu captures."""
+    import torch
+    from paper_1303_2470_gb300 import build, media
+    build.build()
+    from paper_1303_2470_gb300 import mp
+    ctxs = []
+    for n, seed in ((96, 2), (128, 3)):
+        solid, _ = media.random_spheres((n, n, n), [4, 5, 6, 7, 8], 0.42, seed)
+        sd = torch.as_tensor(solid).cuda()
+        u = torch.zeros((3,) + solid.shape, dtype=torch.float32, device="cuda")
+        mp.lb_steady(sd, (1e-3, 0, 0), u, tol=0.0, max_steps=30, check_every=30)
+        Db, ka, kd = media.species(16, seed=seed + 100)
+        ctxs.append(mp.mp_init_batch(sd, u, Db, ka, kd, capacity=16, allow_negative=True))
+    g = mp.mp_group_create(ctxs)
+    mp.mp_group_step(g, 8)
+    torch.cuda.synchronize()
+    print(json.dumps({"profile_batched": "ok", "block": mp.mp_group_block_size(g)}))
+    g.close()
+    return 0
+
+
 def run_profile_case():
     """The workload's kernels on the same 128^3 medium, briefly, for ncu --set full
     captures (python bench.py --profile): LB launches 1-30, k_init, MP launches 1-20."""
@@ -316,6 +339,8 @@ def main():
     ap.add_argument("--workload", default="porous128", choices=["porous128", "batched"],
                     help="porous128: the single-species 128^3 job (the bench line); batched: three "
                          "media x 16 species, grouped launch vs one species per launch")
+    ap.add_argument("--profile-batched", action="store_true",
+                    help="short grouped run (96^3 and 128^3 media x 16 species) for ncu captures")
     ap.add_argument("--profile", action="store_true",
                     help="short run of the same medium and kernels for ncu captures: 30 LB steps, "
                          "mp_init and 20 MP steps, no timing")
@@ -325,6 +350,8 @@ def main():
         return run_reference(args)
     if args.profile:
         return run_profile_case()
+    if args.profile_batched:
+        return run_profile_batched()
     if args.workload == "batched":
         return run_batched(args)
 

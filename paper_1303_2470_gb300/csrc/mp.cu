@@ -67,10 +67,44 @@ struct alignas(FP * sizeof(T)) FieldVec {
     T v[FP];
 };
 
+// 32-byte records of eight FP32 values move as one 256-bit access (ld/st.global.v8.f32):
+// with records scattered over the fluid list, two 16-byte halves would each cost a full
+// L1 sector request per lane
+template <typename T, int W>
+__device__ __forceinline__ FieldVec<T, W> ld_rec(const FieldVec<T, W>* p)
+{
+    return *p;
+}
+template <>
+__device__ __forceinline__ FieldVec<float, 8> ld_rec<float, 8>(const FieldVec<float, 8>* p)
+{
+    FieldVec<float, 8> r;
+    asm("ld.global.v8.f32 {%0,%1,%2,%3,%4,%5,%6,%7}, [%8];"
+        : "=f"(r.v[0]), "=f"(r.v[1]), "=f"(r.v[2]), "=f"(r.v[3]), "=f"(r.v[4]), "=f"(r.v[5]), "=f"(r.v[6]),
+          "=f"(r.v[7])
+        : "l"(p));
+    return r;
+}
+template <typename T, int W>
+__device__ __forceinline__ void st_rec(FieldVec<T, W>* p, const FieldVec<T, W>& r)
+{
+    *p = r;
+}
+template <>
+__device__ __forceinline__ void st_rec<float, 8>(FieldVec<float, 8>* p, const FieldVec<float, 8>& r)
+{
+    asm volatile("st.global.v8.f32 [%0], {%1,%2,%3,%4,%5,%6,%7,%8};" ::"l"(p), "f"(r.v[0]), "f"(r.v[1]), "f"(r.v[2]),
+                 "f"(r.v[3]), "f"(r.v[4]), "f"(r.v[5]), "f"(r.v[6]), "f"(r.v[7])
+                 : "memory");
+}
+
 template <typename T>
 struct Args {
     int nx, ny, nz, N, NF, NI;
-    int FP;  // padded field count of the [species][node][field] layout: 2 or 4
+    int FP;  // fields per species record, padded: 2 or 4
+    int SP;  // species, padded to a whole number of chunks (1 for one species)
+    int SC;  // species per chunk (1 for one species, else 8 / FP); element (n, s, f) sits at
+             // (((s / SC) * rows + n) * SC + s % SC) * FP + f, rows = N for P, NI for P_ads
     Div dx, dxy;  // division by nx and by nx*ny
     const uint32_t* iface;
     const int32_t* ibase;
@@ -82,6 +116,8 @@ struct Args {
     T hl[MP_MAX_SPECIES];  // lambda/2
     T pa[MP_MAX_SPECIES];
     T pd[MP_MAX_SPECIES];
+    T whf[MP_MAX_SPECIES];  // w_face * lambda/2, correctly rounded (the diffusive part of p)
+    T whe[MP_MAX_SPECIES];  // w_edge * lambda/2
     double* partials;      // [gridDim.x][K]
     unsigned int* ticket;  // blocks done in the current launch
     double* Z;             // [K_series][cap]
@@ -100,6 +136,13 @@ struct InitExtra {
 __device__ __forceinline__ bool bit_of(const uint32_t* __restrict__ w, int n)
 {
     return (__ldg(w + (n >> 5)) >> (n & 31)) & 1u;
+}
+
+// element (row, species, field) of a chunk-major field array with `rows` rows
+template <typename T>
+__device__ __forceinline__ size_t elem(const Args<T>& a, size_t rows, size_t row, int sp, int f)
+{
+    return ((((size_t)(sp / a.SC)) * rows + row) * a.SC + (size_t)(sp % a.SC)) * a.FP + f;
 }
 
 template <typename T>
@@ -371,58 +414,150 @@ __device__ __forceinline__ void step_body(const Args<T>& a, int blk, int nblk, c
             }
         }
     } else {
-        Node<T> d;
-        if (active) load_node<T>(a, k, d);
-        for (int sp = 0; sp < a.S; ++sp) {
-            const T hl = a.hl[sp], pa = a.pa[sp], pd = a.pd[sp];
-            T zv[kMaxF - 1] = {T(0), T(0), T(0)};
-            if (active) {
-                T pin[kQ], pout[kQ];
-                species_probs(d, hl, pin, pout);
-                const V* Ps = Pv + (size_t)sp * a.N;
-                const V xr = Ps[d.n];
-                T delta[FP];
+        // Several species, in 32-byte chunks of kSC species x FP fields stored chunk-major
+        // ([chunk][node]): a warp's chunk loads of consecutive fluid nodes are consecutive.
+        // A pass covers up to kCP chunks (8 species of density + one moment); inside it the
+        // link loop is outermost: the flow-dependent part of the link probability is computed
+        // once per link and every neighbour chunk is fetched once, serving all its species.
+        constexpr int kSC = 8 / FP;
+        constexpr int kCP = 2;
+        constexpr int kMaxPass = MP_MAX_SPECIES / (kCP * kSC);
+        using VC = FieldVec<T, kSC * FP>;
+        // per-species constants staged in shared memory, read with compile-time indices
+        __shared__ T s_whf[MP_MAX_SPECIES], s_whe[MP_MAX_SPECIES], s_hl[MP_MAX_SPECIES], s_pa[MP_MAX_SPECIES],
+            s_pd[MP_MAX_SPECIES];
+        for (int j = threadIdx.x; j < MP_MAX_SPECIES; j += kB) {
+            s_whf[j] = a.whf[j];
+            s_whe[j] = a.whe[j];
+            s_hl[j] = a.hl[j];
+            s_pa[j] = a.pa[j];
+            s_pd[j] = a.pd[j];
+        }
+        __syncthreads();
+        const VC* __restrict__ Pc = reinterpret_cast<const VC*>(P);
+        VC* __restrict__ Pnc = reinterpret_cast<VC*>(Pn);
+        const VC* __restrict__ Ac = reinterpret_cast<const VC*>(A);
+        VC* __restrict__ Anc = reinterpret_cast<VC*>(An);
+        const int cpn = a.SP / kSC;  // chunks per node
+        int n = 0, aidx = 0;
+        uint32_t mask = 0;
+        Nbr b{};
+        Flow4<T> ur{T(0), T(0), T(0), T(0)};
+        if (active) {
+            n = __ldg(a.flist + k);
+            mask = __ldg(a.fmask + k);
+            b = node_nbrs(a, n);
+            ur = a.u4[n];
+            if (mask != kAllLinks) aidx = iface_index(a, n);
+        }
 #pragma unroll
-                for (int f = 0; f < FP; ++f) delta[f] = T(0);
+        for (int pass = 0; pass < kMaxPass; ++pass) {
+            const int c0 = pass * kCP;
+            if (c0 >= cpn) break;
+            const int nc = cpn - c0 < kCP ? cpn - c0 : kCP;
+            VC xr[kCP];
+            T delta[kCP][kSC * FP];
+            // u*_g of species s is UA_g + lambda_s/2 UW_g, sums over the open outgoing links
+            T UA[3] = {T(0), T(0), T(0)}, UW[3] = {T(0), T(0), T(0)};
+            if (active) {
+#pragma unroll
+                for (int cc = 0; cc < kCP; ++cc) {
+                    if (cc < nc) xr[cc] = ld_rec(Pc + (size_t)(c0 + cc) * a.N + n);
+#pragma unroll
+                    for (int j = 0; j < kSC * FP; ++j) delta[cc][j] = T(0);
+                }
 #pragma unroll
                 for (int i = 1; i < kQ; ++i) {
-                    if (d.src[i] >= 0) {
-                        const V xs = Ps[d.src[i]];
+                    if ((mask >> (i - 1)) & 1u) {
+                        const int s = src_of(b, i);
+                        const Flow4<T> uf = a.u4[s];
+                        const T qin = qlink(edot<T>(i, uf.x, uf.y, uf.z), uf.w);
+                        const T qout = qlink(edot<T>(opposite(i), ur.x, ur.y, ur.z), ur.w);
 #pragma unroll
-                        for (int f = 0; f < FP; ++f)
-                            delta[f] = rn_add(delta[f], rn_sub(rn_mul(pin[i], xs.v[f]), rn_mul(pout[i], xr.v[f])));
-                    }
-                }
-                if (d.itf) {
-                    const size_t ai = (size_t)sp * a.NI + d.aidx;
-                    const V xa = Av[ai];
-                    V xan;
+                        for (int g = 0; g < 3; ++g) {
+                            const int c = ci(opposite(i), g);
+                            if (c != 0) {
+                                UA[g] += T(c) * weight<T>(i) * qout;
+                                UW[g] += T(c) * weight<T>(i);
+                            }
+                        }
 #pragma unroll
-                    for (int f = 0; f < FP; ++f) {
-                        const T js = rn_sub(rn_mul(pa, xr.v[f]), rn_mul(pd, xa.v[f]));
-                        delta[f] = rn_sub(delta[f], js);
-                        xan.v[f] = rn_add(xa.v[f], js);
-                    }
-                    Anv[ai] = xan;
-                }
-                V xn;
+                        for (int cc = 0; cc < kCP; ++cc) {
+                            if (cc < nc) {
+                                const VC xs = ld_rec(Pc + (size_t)(c0 + cc) * a.N + s);
 #pragma unroll
-                for (int f = 0; f < FP; ++f) xn.v[f] = rn_add(xr.v[f], delta[f]);
-                Pnv[(size_t)sp * a.N + d.n] = xn;
+                                for (int q = 0; q < kSC; ++q) {
+                                    const int sp = (c0 + cc) * kSC + q;
+                                    const T whl = is_face(i) ? s_whf[sp] : s_whe[sp];
+                                    const T pin = rn_fma(weight<T>(i), qin, whl);
+                                    const T pout = rn_fma(weight<T>(i), qout, whl);
 #pragma unroll
-                for (int m = 0; m < kMaxF - 1; ++m) {
-                    if (m < a.M && 1 + m < FP) {
-                        T us, us2;
-                        mean_step(pout, a.dir[m], us, us2);
-                        zv[m] = xn.v[(1 + m) < FP ? 1 + m : 0] * us;
+                                    for (int f = 0; f < FP; ++f) {
+                                        const int j = q * FP + f;
+                                        delta[cc][j] = rn_add(delta[cc][j],
+                                                              rn_sub(rn_mul(pin, xs.v[j]), rn_mul(pout, xr[cc].v[j])));
+                                    }
+                                }
+                            }
+                        }
                     }
                 }
             }
+            // finish each chunk: sorption, store, Z terms and their warp sums
 #pragma unroll
-            for (int m = 0; m < kMaxF - 1; ++m) {
-                if (m < a.M) {
-                    const T w = warp_sum(zv[m]);
-                    if (lane == 0) s_part[warp][sp * a.M + m] = (double)w;
+            for (int cc = 0; cc < kCP; ++cc) {
+                T zv[kSC][kMaxF - 1];
+#pragma unroll
+                for (int q = 0; q < kSC; ++q)
+#pragma unroll
+                    for (int m = 0; m < kMaxF - 1; ++m) zv[q][m] = T(0);
+                if (active && cc < nc) {
+                    if (mask != kAllLinks) {
+                        const size_t ai = (size_t)(c0 + cc) * a.NI + aidx;
+                        const VC xa = ld_rec(Ac + ai);
+                        VC xan;
+#pragma unroll
+                        for (int q = 0; q < kSC; ++q) {
+                            const int sp = (c0 + cc) * kSC + q;
+                            const T pa = s_pa[sp], pd = s_pd[sp];
+#pragma unroll
+                            for (int f = 0; f < FP; ++f) {
+                                const int j = q * FP + f;
+                                const T js = rn_sub(rn_mul(pa, xr[cc].v[j]), rn_mul(pd, xa.v[j]));
+                                delta[cc][j] = rn_sub(delta[cc][j], js);
+                                xan.v[j] = rn_add(xa.v[j], js);
+                            }
+                        }
+                        st_rec(Anc + ai, xan);
+                    }
+                    VC xn;
+#pragma unroll
+                    for (int j = 0; j < kSC * FP; ++j) xn.v[j] = rn_add(xr[cc].v[j], delta[cc][j]);
+                    st_rec(Pnc + (size_t)(c0 + cc) * a.N + n, xn);
+#pragma unroll
+                    for (int q = 0; q < kSC; ++q) {
+                        const T h = s_hl[(c0 + cc) * kSC + q];
+#pragma unroll
+                        for (int m = 0; m < kMaxF - 1; ++m) {
+                            if (m < a.M && 1 + m < FP) {
+                                const int g = a.dir[m];
+                                zv[q][m] = xn.v[q * FP + ((1 + m) < FP ? 1 + m : 0)] * (pick(UA, g) + h * pick(UW, g));
+                            }
+                        }
+                    }
+                }
+#pragma unroll
+                for (int q = 0; q < kSC; ++q) {
+                    const int sp = (c0 + cc) * kSC + q;
+                    if (sp < a.S) {
+#pragma unroll
+                        for (int m = 0; m < kMaxF - 1; ++m) {
+                            if (m < a.M) {
+                                const T w = warp_sum(zv[q][m]);
+                                if (lane == 0) s_part[warp][sp * a.M + m] = (double)w;
+                            }
+                        }
+                    }
                 }
             }
         }
@@ -448,8 +583,12 @@ __device__ __forceinline__ void step_body(const Args<T>& a, int blk, int nblk, c
     if (last && threadIdx.x == 0) *tdev = s_t1;
 }
 
+// the multi-species body keeps two 32-byte chunks per link in flight; capping registers so
+// that 768 threads stay resident per SM trades some of that load hoisting for occupancy
+constexpr int min_blocks(bool single, int block) { return single ? 1 : (768 / block > 1 ? 768 / block : 1); }
+
 template <typename T, int FP, bool kSingle>
-__global__ void __launch_bounds__(kThreads)
+__global__ void __launch_bounds__(kThreads, min_blocks(kSingle, kThreads))
     k_step(const Args<T> a, const T* __restrict__ P, T* __restrict__ Pn, const T* __restrict__ A,
            T* __restrict__ An)
 {
@@ -480,7 +619,7 @@ struct GroupArgs {
 };
 
 template <int FP, bool kSingle, int kB>
-__global__ void __launch_bounds__(kB) k_step_group(const GroupArgs g, int phase)
+__global__ void __launch_bounds__(kB, min_blocks(kSingle, kB)) k_step_group(const GroupArgs g, int phase)
 {
     // context of this block; constant indices only, so the parameter array stays in the
     // constant bank
@@ -531,11 +670,11 @@ __global__ void __launch_bounds__(kThreads)
             const T xa0 = (b.uniform || !d.itf) ? T(0) : (T)b.K[sp] * invZ;
             T xn = inw * x0 + stay * x0;
             if (d.itf) {
-                const size_t ai = ((size_t)sp * a.NI + d.aidx) * a.FP;
+                const size_t ai = elem(a, a.NI, d.aidx, sp, 0);
                 xn += pd * xa0;
                 A1[ai] = pa * x0 + (T(1) - pd) * xa0;
             }
-            P1[((size_t)sp * a.N + d.n) * a.FP] = xn;
+            P1[elem(a, a.N, d.n, sp, 0)] = xn;
 #pragma unroll
             for (int m = 0; m < kMaxF - 1; ++m) {
                 if (m < a.M) {
@@ -545,8 +684,8 @@ __global__ void __launch_bounds__(kThreads)
                     for (int i = 1; i < kQ; ++i)
                         if (ci(i, g) != 0) pg += pin[i] * T(ci(i, g));
                     pg *= invZ;
-                    P1[((size_t)sp * a.N + d.n) * a.FP + 1 + m] = pg;
-                    if (d.itf) A1[((size_t)sp * a.NI + d.aidx) * a.FP + 1 + m] = T(0);
+                    P1[elem(a, a.N, d.n, sp, 1 + m)] = pg;
+                    if (d.itf) A1[elem(a, a.NI, d.aidx, sp, 1 + m)] = T(0);
                     T us, us2;
                     mean_step(pout, g, us, us2);
                     zp[2 * m] = invZ * us2;
@@ -601,17 +740,17 @@ __global__ void __launch_bounds__(kThreads)
 // sum_I P.
 template <typename T>
 __global__ void __launch_bounds__(kThreads)
-    k_mass(const Args<T> a, const T* __restrict__ P, const T* __restrict__ A, double* __restrict__ out)
+    k_mass(const Args<T> a, int sp, const T* __restrict__ P, const T* __restrict__ A, double* __restrict__ out)
 {
     const int k = blockIdx.x * kThreads + threadIdx.x;
     double v[3] = {0.0, 0.0, 0.0};
     if (k < a.NF) {
         const int n = __ldg(a.flist + k);
-        v[0] = (double)P[(size_t)n * a.FP];
+        v[0] = (double)P[elem(a, a.N, n, sp, 0)];
         const uint32_t bits = __ldg(a.iface + (n >> 5));
         if ((bits >> (n & 31)) & 1u) {
             const int j = __ldg(a.ibase + (n >> 5)) + __popc(bits & ((1u << (n & 31)) - 1u));
-            v[1] = (double)A[(size_t)j * a.FP];
+            v[1] = (double)A[elem(a, a.NI, j, sp, 0)];
             v[2] = v[0];
         }
     }
@@ -695,7 +834,9 @@ struct mp_ctx {
     long long n_neg_links = 0, n_neg_stay = 0;
     std::vector<int32_t> ilist;
     size_t elem = 4;
-    int FP = 2;  // fields per node in the [species][node][field] layout (F padded to 2 or 4)
+    int FP = 2;  // fields per species record (F padded to 2 or 4)
+    int SP = 1;  // species padded to whole chunks (1 for one species)
+    int SC = 1;  // species per chunk
     mp_group* owner = nullptr;  // set while the context steps as part of a group
 };
 
@@ -713,6 +854,8 @@ Args<T> make_args(const mp_ctx* c)
     a.NF = (int)c->geo.n_fluid;
     a.NI = (int)c->geo.n_iface;
     a.FP = c->FP;
+    a.SP = c->SP;
+    a.SC = c->SC;
     a.dx = make_div((unsigned)c->geo.nx);
     a.dxy = make_div((unsigned)(c->geo.nx * c->geo.ny));
     a.iface = c->geo.iface;
@@ -726,6 +869,8 @@ Args<T> make_args(const mp_ctx* c)
     for (int m = 0; m < 3; ++m) a.dir[m] = c->dir[m];
     for (int s = 0; s < c->S; ++s) {
         a.hl[s] = (T)(6.0 * c->Db[s]);  // lambda/2 = 12 D_b / 2
+        a.whf[s] = (T)((double)weight<T>(1) * (double)a.hl[s]);
+        a.whe[s] = (T)((double)weight<T>(5) * (double)a.hl[s]);
         a.pa[s] = (T)c->ka[s];
         a.pd[s] = (T)c->kd[s];
     }
@@ -762,8 +907,11 @@ int init_typed(mp_ctx* c, const float* u_in, int init_density)
     const int N = c->geo.N;
     const size_t NI = (size_t)(c->geo.n_iface > 0 ? c->geo.n_iface : 1);
     c->FP = c->F <= 2 ? 2 : 4;
-    const size_t fieldN = (size_t)c->S * N * c->FP;
-    const size_t fieldA = (size_t)c->S * NI * c->FP;
+    const int chunk = 8 / c->FP;  // species per 32-byte chunk of a node record
+    c->SP = c->S == 1 ? 1 : (c->S + chunk - 1) / chunk * chunk;
+    c->SC = c->S == 1 ? 1 : chunk;
+    const size_t fieldN = (size_t)c->SP * N * c->FP;
+    const size_t fieldA = (size_t)c->SP * NI * c->FP;
     const int Kser = c->S * c->M;
     c->elem = sizeof(T);
     c->blocks = (int)((c->geo.n_fluid + kThreads - 1) / kThreads);
@@ -849,10 +997,9 @@ template <typename T>
 int mass_typed(mp_ctx* c, int sp, double out[3])
 {
     Args<T> a = make_args<T>(c);
-    const T* P = (const T*)c->P[c->cur] + (size_t)sp * c->geo.N * c->FP;
-    const size_t NI = (size_t)(c->geo.n_iface > 0 ? c->geo.n_iface : 1);
-    const T* A = (const T*)c->A[c->cur] + (size_t)sp * NI * c->FP;
-    k_mass<T><<<c->blocks, kThreads, 0, c->stream>>>(a, P, A, c->partials);
+    const T* P = (const T*)c->P[c->cur];
+    const T* A = (const T*)c->A[c->cur];
+    k_mass<T><<<c->blocks, kThreads, 0, c->stream>>>(a, sp, P, A, c->partials);
     std::vector<double> h((size_t)c->blocks * 3);
     MP_CUDA(cudaGetLastError());
     MP_CUDA(cudaMemcpyAsync(h.data(), c->partials, h.size() * sizeof(double), cudaMemcpyDeviceToHost, c->stream));
@@ -1076,15 +1223,16 @@ int mp_get_field(mp_ctx* c, int species, int field, double* free_dense, double* 
     }
     const size_t N = (size_t)c->geo.N;
     const size_t NI = (size_t)(c->geo.n_iface > 0 ? c->geo.n_iface : 1);
-    const size_t FP = (size_t)c->FP, E = c->elem;
-    std::vector<char> buf(N * FP * E), abuf(NI * FP * E);
-    MP_CUDA(cudaMemcpyAsync(buf.data(), (char*)c->P[c->cur] + (size_t)species * N * FP * E, N * FP * E,
-                            cudaMemcpyDeviceToHost, c->stream));
-    MP_CUDA(cudaMemcpyAsync(abuf.data(), (char*)c->A[c->cur] + (size_t)species * NI * FP * E, NI * FP * E,
-                            cudaMemcpyDeviceToHost, c->stream));
+    const size_t FP = (size_t)c->FP, SP = (size_t)c->SP, E = c->elem;
+    std::vector<char> buf(N * SP * FP * E), abuf(NI * SP * FP * E);
+    MP_CUDA(cudaMemcpyAsync(buf.data(), c->P[c->cur], buf.size(), cudaMemcpyDeviceToHost, c->stream));
+    MP_CUDA(cudaMemcpyAsync(abuf.data(), c->A[c->cur], abuf.size(), cudaMemcpyDeviceToHost, c->stream));
     MP_CUDA(cudaStreamSynchronize(c->stream));
+    const size_t SC = (size_t)c->SC;
     auto at = [&](const std::vector<char>& v, size_t i) {
-        return E == 8 ? ((const double*)v.data())[i * FP + field] : (double)((const float*)v.data())[i * FP + field];
+        const size_t rows = &v == &buf ? N : NI;
+        const size_t j = ((((size_t)species / SC) * rows + i) * SC + (size_t)species % SC) * FP + (size_t)field;
+        return E == 8 ? ((const double*)v.data())[j] : (double)((const float*)v.data())[j];
     };
     for (size_t n = 0; n < N; ++n) free_dense[n] = at(buf, n);
     if (ads_dense) {
@@ -1104,26 +1252,27 @@ int mp_set_field(mp_ctx* c, int species, int field, const double* free_dense, co
     }
     const size_t N = (size_t)c->geo.N;
     const size_t NI = (size_t)(c->geo.n_iface > 0 ? c->geo.n_iface : 1);
-    const size_t FP = (size_t)c->FP, E = c->elem;
-    // read the species' slab, replace one field, write it back; solid nodes stay zero
+    const size_t FP = (size_t)c->FP, SP = (size_t)c->SP, E = c->elem;
+    // read the node records, replace one species' field, write them back; solids stay zero
     std::vector<uint32_t> fl((size_t)c->geo.W);
-    std::vector<char> buf(N * FP * E), abuf(NI * FP * E);
-    char* dP = (char*)c->P[c->cur] + (size_t)species * N * FP * E;
-    char* dA = (char*)c->A[c->cur] + (size_t)species * NI * FP * E;
+    std::vector<char> buf(N * SP * FP * E), abuf(NI * SP * FP * E);
     MP_CUDA(cudaMemcpyAsync(fl.data(), c->geo.fluid, fl.size() * 4, cudaMemcpyDeviceToHost, c->stream));
-    MP_CUDA(cudaMemcpyAsync(buf.data(), dP, N * FP * E, cudaMemcpyDeviceToHost, c->stream));
-    MP_CUDA(cudaMemcpyAsync(abuf.data(), dA, NI * FP * E, cudaMemcpyDeviceToHost, c->stream));
+    MP_CUDA(cudaMemcpyAsync(buf.data(), c->P[c->cur], buf.size(), cudaMemcpyDeviceToHost, c->stream));
+    MP_CUDA(cudaMemcpyAsync(abuf.data(), c->A[c->cur], abuf.size(), cudaMemcpyDeviceToHost, c->stream));
     MP_CUDA(cudaStreamSynchronize(c->stream));
+    const size_t SC = (size_t)c->SC;
     auto put = [&](std::vector<char>& v, size_t i, double x) {
+        const size_t rows = &v == &buf ? N : NI;
+        const size_t j = ((((size_t)species / SC) * rows + i) * SC + (size_t)species % SC) * FP + (size_t)field;
         if (E == 8)
-            ((double*)v.data())[i * FP + field] = x;
+            ((double*)v.data())[j] = x;
         else
-            ((float*)v.data())[i * FP + field] = (float)x;
+            ((float*)v.data())[j] = (float)x;
     };
     for (size_t n = 0; n < N; ++n) put(buf, n, ((fl[n >> 5] >> (n & 31)) & 1u) ? free_dense[n] : 0.0);
     for (size_t k = 0; k < c->ilist.size(); ++k) put(abuf, k, ads_dense ? ads_dense[c->ilist[k]] : 0.0);
-    MP_CUDA(cudaMemcpyAsync(dP, buf.data(), N * FP * E, cudaMemcpyHostToDevice, c->stream));
-    MP_CUDA(cudaMemcpyAsync(dA, abuf.data(), NI * FP * E, cudaMemcpyHostToDevice, c->stream));
+    MP_CUDA(cudaMemcpyAsync(c->P[c->cur], buf.data(), buf.size(), cudaMemcpyHostToDevice, c->stream));
+    MP_CUDA(cudaMemcpyAsync(c->A[c->cur], abuf.data(), abuf.size(), cudaMemcpyHostToDevice, c->stream));
     MP_CUDA(cudaStreamSynchronize(c->stream));
     return MP_OK;
 }
@@ -1221,8 +1370,8 @@ int group_autotune(mp_group* g, int steps)
     for (size_t c = 0; c < g->ctx.size() && rc == MP_OK; ++c) {
         mp_ctx* x = g->ctx[c];
         const size_t NI = (size_t)(x->geo.n_iface > 0 ? x->geo.n_iface : 1);
-        nP[c] = (size_t)x->S * x->geo.N * x->FP * sizeof(float);
-        nA[c] = (size_t)x->S * NI * x->FP * sizeof(float);
+        nP[c] = (size_t)x->SP * x->geo.N * x->FP * sizeof(float);
+        nA[c] = (size_t)x->SP * NI * x->FP * sizeof(float);
         if (cudaMalloc(&bP[c], nP[c]) != cudaSuccess || cudaMalloc(&bA[c], nA[c]) != cudaSuccess) {
             (void)cudaGetLastError();
             set_error("autotune: no device memory for the state backup");
