@@ -66,8 +66,10 @@ def test_group_equals_separate_contexts(mp, graph_steps, autotune, single, direc
             for d in ({"x": [0], "xz": [0, 2]}[directions]):
                 Za, Da = mp.mp_vacf(c_ref, s, d)
                 Zb, Db_ = mp.mp_vacf(c_grp, s, d)
-                assert np.allclose(Za, Zb, rtol=1e-12, atol=1e-18)
-                assert np.allclose(Da, Db_, rtol=1e-12, atol=1e-18)
+                # identical fields; the Z sums may group the FP32 node terms differently
+                # (block size, or the tiled single-species kernel of separate contexts)
+                assert np.max(np.abs(Za - Zb)) <= 1e-7 * abs(Za[0])
+                assert np.max(np.abs(Da - Db_) / np.abs(Da)) <= 1e-7
     g.close()
     for c in ref + grp:
         c.close()
