@@ -355,7 +355,7 @@ __device__ __forceinline__ void step_body(const Args<T>& a, int blk, int nblk, c
     const bool active = k < a.NF;
     const int K = a.S * a.M;
 
-    if (kSingle) {
+    if constexpr (kSingle) {
         const T hl = a.hl[0], pa = a.pa[0], pd = a.pd[0];
         T zv[kMaxF - 1] = {T(0), T(0), T(0)};
         if (active) {
@@ -585,13 +585,21 @@ __device__ __forceinline__ void step_body(const Args<T>& a, int blk, int nblk, c
 
 // the multi-species body keeps two 32-byte chunks per link in flight; capping registers so
 // that 768 threads stay resident per SM trades some of that load hoisting for occupancy
-constexpr int min_blocks(bool single, int block) { return single ? 1 : (768 / block > 1 ? 768 / block : 1); }
+// (the single-species body fits in 32 registers, i.e. full occupancy at 256 threads)
+// (FP32: the single-species body fits in 32 registers, full occupancy at 256 threads;
+// FP64 needs twice the registers and is left uncapped)
+constexpr int min_blocks(bool single, int block, int elem)
+{
+    return elem == 8 ? 1 : (single ? 2048 / block : (768 / block > 1 ? 768 / block : 1));
+}
 
 template <typename T, int FP, bool kSingle>
-__global__ void __launch_bounds__(kThreads, min_blocks(kSingle, kThreads))
-    k_step(const Args<T> a, const T* __restrict__ P, T* __restrict__ Pn, const T* __restrict__ A,
-           T* __restrict__ An)
+__global__ void __launch_bounds__(kThreads, min_blocks(kSingle, kThreads, sizeof(T)))
+    k_step(const __grid_constant__ Args<T> a, const T* __restrict__ P, T* __restrict__ Pn,
+           const T* __restrict__ A, T* __restrict__ An)
 {
+    // __grid_constant__: step_body reads the arguments through a reference, straight from
+    // the constant bank (without it the whole structure would be copied per thread)
     step_body<T, FP, kSingle, kThreads>(a, blockIdx.x, gridDim.x, P, Pn, A, An);
 }
 
@@ -619,7 +627,8 @@ struct GroupArgs {
 };
 
 template <int FP, bool kSingle, int kB>
-__global__ void __launch_bounds__(kB, min_blocks(kSingle, kB)) k_step_group(const GroupArgs g, int phase)
+__global__ void __launch_bounds__(kB, kSingle ? 1536 / kB : min_blocks(false, kB, 4))
+    k_step_group(const GroupArgs g, int phase)
 {
     // context of this block; constant indices only, so the parameter array stays in the
     // constant bank
