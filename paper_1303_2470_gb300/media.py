@@ -4,9 +4,9 @@ This module holds none of the moment-propagation arithmetic; it only makes the i
 that both the GPU library and the FP64 oracle are fed. All arrays use the lattice layout
 of the library: shape (nz, ny, nx), x fastest, periodic on every axis, solid = 1.
 
-Geometries follow the media of the paper: the slit pore of its validation section and
-porous solids (the paper's fcc sphere packing is replaced by randomly placed, overlapping
-spheres, a Boolean model, for the porous-medium workloads).
+Geometries follow the media of the paper: the slit pore of its validation section, the
+compact face-centred cubic packing of spheres of its porous-medium example, and, for the
+large porous-medium workloads, randomly placed overlapping spheres (a Boolean model).
 """
 from __future__ import annotations
 
@@ -25,6 +25,28 @@ def slit(nx: int, ny: int, H: int) -> np.ndarray:
 def bulk(nx: int, ny: int, nz: int) -> np.ndarray:
     """Periodic box with no solid."""
     return np.zeros((nz, ny, nx), dtype=np.uint8)
+
+
+def fcc(a: int, radius: float | None = None) -> np.ndarray:
+    """One periodic unit cell of a face-centred cubic packing of spheres (Sec. Validation,
+    the fcc example): lattice parameter a nodes, sphere centres at the cell corner and the
+    three face centres, (0,0,0), (a/2,a/2,0), (a/2,0,a/2), (0,a/2,a/2), with their periodic
+    images. radius defaults to the compact (touching) packing, a sqrt(2)/4, whose continuum
+    porosity is 1 - pi/(3 sqrt 2) ~ 0.26. Node (x,y,z) sits at integer coordinates and is
+    solid when its minimum-image distance to a centre is < radius. Returns solid[a,a,a]."""
+    R = a * np.sqrt(2.0) / 4.0 if radius is None else float(radius)
+    g = np.arange(a, dtype=np.float64)
+    centres = np.array([[0.0, 0.0, 0.0], [a / 2, a / 2, 0.0], [a / 2, 0.0, a / 2], [0.0, a / 2, a / 2]])
+    solid = np.zeros((a, a, a), dtype=bool)
+    for cx, cy, cz in centres:
+        dx = np.abs(g - cx)
+        dx = np.minimum(dx, a - dx)
+        dy = np.abs(g - cy)
+        dy = np.minimum(dy, a - dy)
+        dz = np.abs(g - cz)
+        dz = np.minimum(dz, a - dz)
+        solid |= (dz[:, None, None] ** 2 + dy[None, :, None] ** 2 + dx[None, None, :] ** 2) < R * R
+    return solid.astype(np.uint8)
 
 
 def random_spheres(shape, radius, porosity: float, seed: int, max_spheres: int = 10_000_000):

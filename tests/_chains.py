@@ -221,3 +221,42 @@ def walkers(ch, pi0, nwalk, tmax, seed):
         steps[t] = dis[state, k].T
         state = tgt[state, k]
     return steps
+
+
+
+def zchain_D(ch, pi0, g, ts, confined=False):
+    """D_g(t) = Z(0)/2 + sum_{m=1}^t Z(m) of a z-chain at the integer times ts, summed in
+    closed form over the eigenvalues mu_k of the transition matrix. With Z(m) =
+    sum_k a_k mu_k^(m-1) (a_k from the eigen-expansion of the chain started from pi0):
+        D(t) = Z(0)/2 + sum_k a_k (1 - mu_k^t)/(1 - mu_k)      (mu_k = 1 terms: a_k t).
+    confined=True (a direction in which the tracer cannot leave, so D(inf) = 0) sums only
+    the decaying tails, D(t) = -sum_{mu_k != 1} a_k mu_k^t/(1 - mu_k), which keeps full
+    relative accuracy where D(t) has decayed by many orders. A chain reversible with respect
+    to pi0 (u = 0) is diagonalised symmetrically."""
+    V = ch.Vg[g]
+    m = V.sum(1)
+    Z0 = pi0 @ ch.V2g[g].sum(1)
+    w = pi0 @ V
+    live = pi0 > 0.0                      # states the start can reach (no adsorbed ones if k_a = 0)
+    P = pi0[live, None] * ch.T[np.ix_(live, live)]
+    if np.max(np.abs(P - P.T)) < 1e-15:
+        # S = Pi^(1/2) T Pi^(-1/2) is symmetric: T = Pi^(-1/2) Q diag(mu) Q^T Pi^(1/2)
+        r = np.sqrt(pi0[live])
+        mu, Q = np.linalg.eigh(ch.T[np.ix_(live, live)] * r[:, None] / r[None, :])
+        a = ((w[live] / r) @ Q) * (Q.T @ (r * m[live]))
+    else:
+        mu, R = np.linalg.eig(ch.T.T)     # columns: left eigenvectors of T
+        a = np.linalg.solve(R, w) * (R.T @ m)
+    mu = mu.astype(np.complex128)
+    a = a.astype(np.complex128)
+    one = np.abs(1.0 - mu) < 1e-12
+    ts = np.asarray(ts, dtype=np.float64)
+    out = np.empty(ts.shape)
+    for j, t in enumerate(ts):
+        if confined:
+            tail = a[~one] * mu[~one] ** t / (1.0 - mu[~one])
+            out[j] = -np.real(np.sum(tail))
+        else:
+            geo = np.where(one, t, (1.0 - mu ** t) / np.where(one, 1.0, 1.0 - mu))
+            out[j] = Z0 / 2.0 + np.real(np.sum(a * geo))
+    return out

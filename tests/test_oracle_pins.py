@@ -14,6 +14,7 @@ import numpy as np
 import pytest
 
 import oracle
+from oracle import continuum as oc
 import _chains as chains
 from paper_1303_2470_gb300 import media
 
@@ -240,12 +241,6 @@ def test_stationary_slit_walkers_give_D_of_t():
         assert abs(est - target) < 4 * se
 
 
-def _taylor_aris(Pe, y, D_b, L, kd, leading):
-    lead = 1.0 if leading == "printed" else 1.0 / (1.0 + 2.0 * y)
-    extra = 0.0 if y == 0 else (D_b / (L * L * kd)) * 2.0 * y / (1.0 + 2.0 * y) ** 3
-    return lead + Pe ** 2 * ((102 * y * y + 18 * y + 1) / (210.0 * (1 + 2 * y) ** 3) + extra)
-
-
 @pytest.mark.parametrize("ka,kd", [(0.0, 0.0), (1e-3, 1e-2), (1e-2, 1e-3)])
 def test_taylor_aris_dispersion_of_the_lattice_chain(ka, kd):
     """Eq. exact_K for Poiseuille flow in a slit, H = 32, D_b = 0.02, u_max = 0.05: the
@@ -263,7 +258,7 @@ def test_taylor_aris_dispersion_of_the_lattice_chain(ka, kd):
         y = 0.0 if ka == 0 else ka_H / (kd_H * H)
         vfluid = media.poiseuille_profile(H, umax)[1:H + 1].mean()   # mean flow velocity
         Pe = H * vfluid / D_b
-        exact = D_b * _taylor_aris(Pe, y, D_b, H, kd_H if kd_H > 0 else 1.0, "read")
+        exact = oc.taylor_aris_K(Pe, y, D_b, H, kd_H if kd_H > 0 else 1.0, "read")
         errs.append(abs(K / exact - 1.0))
     assert errs[0] < 0.05
     assert errs[1] < errs[0]
@@ -288,7 +283,7 @@ def test_taylor_aris_refinement_selects_the_leading_term_reading():
         y = ka_H / (kd_H * H)
         Pe = H * media.poiseuille_profile(H, umax)[1:H + 1].mean() / D_b
         for lead in gaps:
-            gaps[lead].append(K / (D_b * _taylor_aris(Pe, y, D_b, H, kd_H, lead)) - 1.0)
+            gaps[lead].append(K / oc.taylor_aris_K(Pe, y, D_b, H, kd_H, lead) - 1.0)
     extrap = {lead: 2 * g[1] - g[0] for lead, g in gaps.items()}
     assert abs(extrap["read"]) < 1e-3
     assert abs(extrap["printed"]) > 4e-3
