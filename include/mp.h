@@ -116,8 +116,11 @@ int mp_init_batch(mp_ctx** out, const mp_geometry* g, const float* u, int n_spec
  * removed from the stay fraction (1 - sum_i p_i - p_a) so that total mass is conserved;
  * then Z_g(t+1) = sum_r P_g(r,t+1) sum_i p_i(r) c_ig (last equation of that section) and
  * D(t+1) = D(t) + Z(t+1) (Eq. D_t_from_vacf as a sum over steps), both in FP64.
- * Asynchronous on the context's stream. Errors: MP_EINVAL (n < 0, or the series would
- * exceed its capacity), MP_ECUDA.
+ * Asynchronous on the context's stream. On a context created with its own stream (not the
+ * legacy or per-thread default stream), calls with n >= 128 replay runs of 64 steps from a
+ * CUDA graph captured at first use (one per starting buffer): the same kernels with the
+ * same arguments, so results are identical; it only removes the per-launch host cost.
+ * Errors: MP_EINVAL (n < 0, or the series would exceed its capacity), MP_ECUDA.
  */
 int mp_step(mp_ctx* c, int64_t n);
 

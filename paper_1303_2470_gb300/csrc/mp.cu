@@ -847,6 +847,9 @@ struct mp_ctx {
     int SP = 1;  // species padded to whole chunks (1 for one species)
     int SC = 1;  // species per chunk
     mp_group* owner = nullptr;  // set while the context steps as part of a group
+    // runs of kCtxGraphSteps steps captured once per starting buffer (cur) and replayed
+    cudaGraph_t graph[2] = {nullptr, nullptr};
+    cudaGraphExec_t exec[2] = {nullptr, nullptr};
 };
 
 namespace {
@@ -895,6 +898,10 @@ Args<T> make_args(const mp_ctx* c)
 void destroy(mp_ctx* c)
 {
     if (!c) return;
+    for (int b = 0; b < 2; ++b) {
+        if (c->exec[b]) cudaGraphExecDestroy(c->exec[b]);
+        if (c->graph[b]) cudaGraphDestroy(c->graph[b]);
+    }
     free_geometry(&c->geo, nullptr, false);
     cudaFree(c->u4);
     cudaFree(c->fmask);
@@ -985,19 +992,48 @@ int init_typed(mp_ctx* c, const float* u_in, int init_density)
     return MP_OK;
 }
 
+// Long runs on a context with its own stream replay a CUDA graph of this many steps (even,
+// so a replay ends on the buffer it started from); the launches are the same as plain ones.
+constexpr int kCtxGraphSteps = 64;
+
+bool capturable(cudaStream_t s)
+{
+    return s != nullptr && s != cudaStreamLegacy && s != cudaStreamPerThread;
+}
+
 template <typename T>
 int step_typed(mp_ctx* c, long long n)
 {
     Args<T> a = make_args<T>(c);
     auto kern = c->FP == 2 ? (c->S == 1 ? k_step<T, 2, true> : k_step<T, 2, false>)
                            : (c->S == 1 ? k_step<T, 4, true> : k_step<T, 4, false>);
-    for (long long k = 0; k < n; ++k) {
-        const int s = c->cur;
-        kern<<<c->blocks, kThreads, 0, c->stream>>>(a, (const T*)c->P[s], (T*)c->P[1 - s], (const T*)c->A[s],
-                                                    (T*)c->A[1 - s]);
-        c->cur = 1 - s;
-        c->t += 1;
+    auto launch = [&](long long count) {
+        for (long long k = 0; k < count; ++k) {
+            const int s = c->cur;
+            kern<<<c->blocks, kThreads, 0, c->stream>>>(a, (const T*)c->P[s], (T*)c->P[1 - s], (const T*)c->A[s],
+                                                        (T*)c->A[1 - s]);
+            c->cur = 1 - s;
+        }
+    };
+    if (capturable(c->stream) && n >= 2 * kCtxGraphSteps) {
+        const int b = c->cur;
+        if (!c->exec[b]) {
+            cudaError_t e = cudaStreamBeginCapture(c->stream, cudaStreamCaptureModeThreadLocal);
+            if (e == cudaSuccess) {
+                launch(kCtxGraphSteps);
+                e = cudaStreamEndCapture(c->stream, &c->graph[b]);
+            }
+            c->cur = b;
+            if (e == cudaSuccess) e = cudaGraphInstantiate(&c->exec[b], c->graph[b], 0);
+            if (e != cudaSuccess) return cuda_fail(e, "mp_step: graph capture");
+        }
+        for (; n >= kCtxGraphSteps; n -= kCtxGraphSteps) {
+            MP_CUDA(cudaGraphLaunch(c->exec[b], c->stream));
+            c->t += kCtxGraphSteps;
+        }
     }
+    launch(n);
+    c->t += n;
     MP_CUDA(cudaGetLastError());
     return MP_OK;
 }
