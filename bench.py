@@ -336,6 +336,9 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--mp-steps", type=int, default=WORKLOAD["mp_steps"])
+    ap.add_argument("--precision", default="fp32", choices=["fp32", "fp16"],
+                    help="field storage of the MP step: fp32 (default) or binary16 with FP32 "
+                         "arithmetic and stochastic rounding")
     ap.add_argument("--workload", default="porous128", choices=["porous128", "batched"],
                     help="porous128: the single-species 128^3 job (the bench line); batched: three "
                          "media x 16 species, grouped launch vs one species per launch")
@@ -396,7 +399,8 @@ def main():
                                         stream=stream)
         ev[1].record(stream)
         ctx = mp.mp_init(solid_arg, u, WORKLOAD["D_b"], WORKLOAD["k_a"], WORKLOAD["k_d"],
-                         capacity=WORKLOAD["mp_steps"] + 2, stream=stream, allow_negative=True)
+                         capacity=WORKLOAD["mp_steps"] + 2, stream=stream, allow_negative=True,
+                         precision=args.precision)
         ev[2].record(stream)
         mp.mp_step(ctx, WORKLOAD["mp_steps"])
         if host_out is not None:
@@ -456,13 +460,17 @@ def main():
     peak, peak_kind = _peaks()
     n_iface = int(info["n_interface"])
     S = WORKLOAD["species"]
-    mp_bytes = n_fluid * (16 * S + 13) + n_iface * 16 * S         # per MP launch
+    eb = 2 if args.precision == "fp16" else 4                     # bytes per stored field value
+    mp_name = "k_step<float,half>" if args.precision == "fp16" else "k_step<float>"
+    # per MP launch: 2 fields read + written per fluid node and species, flow 12 B + flags 1 B
+    # per fluid node, the adsorbed partners' 2 fields read + written per interfacial node
+    mp_bytes = n_fluid * (4 * eb * S + 13) + n_iface * 4 * eb * S
     lb_steps_mean = float(np.mean(lb_steps_all))
     lb_bytes = n_fluid * 19 * 2 * 4                               # per LB launch
     mp_launch_s = mp_ms / 1e3 / (args.steps * WORKLOAD["mp_steps"])
     lb_launch_s = lb_ms / 1e3 / (args.steps * lb_steps_mean)
     kern = {
-        "k_step<float>": {"share": mp_ms / total_ms, "avg_launch_us": mp_launch_s * 1e6,
+        mp_name: {"share": mp_ms / total_ms, "avg_launch_us": mp_launch_s * 1e6,
                           "algorithmic_bytes": mp_bytes, "gbs": mp_bytes / mp_launch_s / 1e9,
                           "src": "mp.cu"},
         "k_lb_step": {"share": lb_ms / total_ms, "avg_launch_us": lb_launch_s * 1e6,
@@ -481,6 +489,8 @@ def main():
         "warmup": args.warmup, "ms_per_step": total_ms_max / args.steps, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
         "config": dict(WORKLOAD, n_fluid=n_fluid, n_interface=n_iface, spheres=nspheres,
+                       **({"precision": "binary16 field storage (stochastic rounding), fp32 arithmetic, "
+                                        "fp64 reductions and D(t)"} if args.precision == "fp16" else {}),
                        negative_links=int(info["n_negative_links"]),
                        force_x=Fx, l2="256 MiB buffer written between timed jobs",
                        parallelism="replicas" if world > 1 else "single GPU"),

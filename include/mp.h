@@ -43,6 +43,21 @@ extern "C" {
 /* ---- storage / arithmetic precision of the propagated fields ------------------------- */
 #define MP_FP32 0 /* FP32 storage and arithmetic, FP64 reductions and D(t) (default)        */
 #define MP_FP64 1 /* FP64 storage, arithmetic and reductions                                */
+/* IEEE binary16 storage of the fields with FP32 arithmetic and FP64 reductions (no
+ * counterpart in the paper: a storage variant that halves the bytes of every field access).
+ * Stored values are scaled per species by the partition function Z_s = N_F + K N_I, so the
+ * equilibrium free density is stored as 1 (no subnormal densities), and narrowed to binary16
+ * after every update either stochastically (MP_ROUND_STOCHASTIC: rounded up in magnitude
+ * with probability equal to the dropped fraction of the spacing, with random bits from a
+ * counter-based hash of the step and the element, so the rounding is unbiased and
+ * reproducible) or to nearest (MP_ROUND_NEAREST, which loses every per-step change below
+ * half a spacing). Z, D, mp_mass and the field I/O are unscaled. Needs K = k_a/k_d <= 30000
+ * (adsorbed values must stay below the binary16 maximum); not available in groups. */
+#define MP_FP16 2
+
+/* ---- rounding of binary16 storage (mp_options.rounding) ------------------------------- */
+#define MP_ROUND_STOCHASTIC 0
+#define MP_ROUND_NEAREST 1
 
 /* ---- initial density field ------------------------------------------------------------ */
 #define MP_INIT_EQUILIBRIUM 0 /* Boltzmann weights of Sec. "Algorithm" (free + adsorbed)    */
@@ -59,7 +74,7 @@ typedef struct {
 
 /* Options of an MP context; mp_default_options() fills the defaults. */
 typedef struct {
-    int precision;      /* MP_FP32 (default) or MP_FP64                                      */
+    int precision;      /* MP_FP32 (default), MP_FP64 or MP_FP16                             */
     int directions;     /* velocity moments to propagate, bit mask 1 = x, 2 = y, 4 = z;
                            0 means x only                                                   */
     int init_density;   /* MP_INIT_EQUILIBRIUM (default) or MP_INIT_UNIFORM                 */
@@ -69,6 +84,7 @@ typedef struct {
     int64_t capacity;   /* time points kept in the device Z(t)/D(t) series, >= 2;
                            0 means 131072. mp_step fails once the series is full.           */
     void* stream;       /* cudaStream_t of all work of the context; NULL = default stream   */
+    int rounding;       /* MP_FP16 only: MP_ROUND_STOCHASTIC (default) or MP_ROUND_NEAREST  */
 } mp_options;
 
 void mp_default_options(mp_options* opt);

@@ -24,7 +24,10 @@
 #include <cstdio>
 #include <cstring>
 #include <string>
+#include <type_traits>
 #include <vector>
+
+#include <cuda_fp16.h>
 
 #include "internal.cuh"
 #include "link_arith.cuh"
@@ -98,6 +101,91 @@ __device__ __forceinline__ void st_rec<float, 8>(FieldVec<float, 8>* p, const Fi
                  : "memory");
 }
 
+// ---------------------------------------------------------------------------------------
+// Storage type TS of the fields: float or double (the arithmetic type T itself), or IEEE
+// binary16 with FP32 arithmetic. A record is widened to T on load and narrowed on store.
+// Binary16 rounding is to nearest or stochastic: the magnitude is rounded up with
+// probability equal to the dropped fraction of the binary16 spacing, compared against
+// random bits from a counter-based hash of (step, element). Stochastic rounding is
+// unbiased, so per-step changes below half a spacing still move a field on average.
+// ---------------------------------------------------------------------------------------
+__device__ __forceinline__ float widen1(float v) { return v; }
+__device__ __forceinline__ double widen1(double v) { return v; }
+__device__ __forceinline__ float widen1(__half v) { return __half2float(v); }
+
+// 32-bit integer hash "lowbias32" (C. Wellons, "Prospecting for hash functions", 2018)
+__device__ __forceinline__ uint32_t hash32(uint32_t x)
+{
+    x ^= x >> 16;
+    x *= 0x7feb352du;
+    x ^= x >> 15;
+    x *= 0x846ca68bu;
+    x ^= x >> 16;
+    return x;
+}
+
+__device__ __forceinline__ __half half_stochastic(float x, uint32_t r)
+{
+    if (fabsf(x) < 6.103515625e-05f) {
+        // below the smallest normal binary16 the spacing is 2^-24: round q = x 2^24 to an
+        // integer, up with probability q - floor(q); the result is exact in binary16
+        const float q = x * 16777216.0f;
+        const float lo = floorf(q);
+        const float u = (float)(r >> 8) * 5.9604644775390625e-08f;  // uniform in [0, 1)
+        return __float2half_rz((u < q - lo ? lo + 1.0f : lo) * 5.9604644775390625e-08f);
+    }
+    // normal range: binary16 keeps 10 of the 23 FP32 mantissa bits; adding 13 random bits
+    // below the kept ones carries into them with the probability of the dropped fraction
+    const uint32_t b = (__float_as_uint(x) + (r & 0x1fffu)) & ~0x1fffu;
+    return __float2half_rz(__uint_as_float(b));
+}
+
+template <typename TS>
+struct Narrow;
+template <>
+struct Narrow<float> {
+    __device__ static float one(float v, uint32_t, bool) { return v; }
+};
+template <>
+struct Narrow<double> {
+    __device__ static double one(double v, uint32_t, bool) { return v; }
+};
+template <>
+struct Narrow<__half> {
+    __device__ static __half one(float v, uint32_t key, bool stochastic)
+    {
+        return stochastic ? half_stochastic(v, hash32(key)) : __float2half_rn(v);
+    }
+};
+
+template <typename T, typename TS, int W>
+__device__ __forceinline__ FieldVec<T, W> ld_wide(const FieldVec<TS, W>* p)
+{
+    if constexpr (std::is_same<T, TS>::value) {
+        return ld_rec(p);
+    } else {
+        const FieldVec<TS, W> h = *p;
+        FieldVec<T, W> r;
+#pragma unroll
+        for (int j = 0; j < W; ++j) r.v[j] = widen1(h.v[j]);
+        return r;
+    }
+}
+
+// key: distinct per stored element and step (see step_body)
+template <typename T, typename TS, int W>
+__device__ __forceinline__ void st_narrow(FieldVec<TS, W>* p, const FieldVec<T, W>& v, uint32_t key, bool stochastic)
+{
+    if constexpr (std::is_same<T, TS>::value) {
+        st_rec(p, v);
+    } else {
+        FieldVec<TS, W> h;
+#pragma unroll
+        for (int j = 0; j < W; ++j) h.v[j] = Narrow<TS>::one(v.v[j], key + (uint32_t)j, stochastic);
+        *p = h;
+    }
+}
+
 template <typename T>
 struct Args {
     int nx, ny, nz, N, NF, NI;
@@ -118,8 +206,10 @@ struct Args {
     T pd[MP_MAX_SPECIES];
     T whf[MP_MAX_SPECIES];  // w_face * lambda/2, correctly rounded (the diffusive part of p)
     T whe[MP_MAX_SPECIES];  // w_edge * lambda/2
-    double* partials;      // [gridDim.x][K]
-    unsigned int* ticket;  // blocks done in the current launch
+    double zsc[MP_MAX_SPECIES];  // stored value x zsc = field value (1 unless binary16 storage)
+    int stochastic;              // binary16 storage: stochastic rounding (else to nearest)
+    double* partials;            // [gridDim.x][K]
+    unsigned int* ticket;        // blocks done in the current launch
     double* Z;             // [K_series][cap]
     double* D;
     long long* tdev;  // time index of the last written series entry
@@ -130,6 +220,7 @@ struct InitExtra {
     double invZ[MP_MAX_SPECIES];  // 1 / partition function (free weight per fluid node)
     double K[MP_MAX_SPECIES];     // k_a / k_d (0 without sorption)
     double inv_nf;                // 1 / N_fluid
+    double sc[MP_MAX_SPECIES];    // storage scale: stored = field value x sc (1 / zsc)
     int uniform;                  // density starts uniform-free
 };
 
@@ -339,16 +430,21 @@ __device__ __forceinline__ bool grid_total(double* partials, int K, unsigned int
 // and reused by every species. Each warp reduces its Z terms with shuffles into shared
 // memory; the block combines them after one barrier.
 // ---------------------------------------------------------------------------------------
-template <typename T, int FP, bool kSingle, int kB>
-__device__ __forceinline__ void step_body(const Args<T>& a, int blk, int nblk, const T* __restrict__ P,
-                                          T* __restrict__ Pn, const T* __restrict__ A, T* __restrict__ An)
+template <typename T, typename TS, int FP, bool kSingle, int kB>
+__device__ __forceinline__ void step_body(const Args<T>& a, int blk, int nblk, const TS* __restrict__ P,
+                                          TS* __restrict__ Pn, const TS* __restrict__ A, TS* __restrict__ An)
 {
     constexpr int kW = kB / 32;
     using V = FieldVec<T, FP>;
-    const V* __restrict__ Pv = reinterpret_cast<const V*>(P);
-    V* __restrict__ Pnv = reinterpret_cast<V*>(Pn);
-    const V* __restrict__ Av = reinterpret_cast<const V*>(A);
-    V* __restrict__ Anv = reinterpret_cast<V*>(An);
+    using VS = FieldVec<TS, FP>;
+    const VS* __restrict__ Pv = reinterpret_cast<const VS*>(P);
+    VS* __restrict__ Pnv = reinterpret_cast<VS*>(Pn);
+    const VS* __restrict__ Av = reinterpret_cast<const VS*>(A);
+    VS* __restrict__ Anv = reinterpret_cast<VS*>(An);
+    // binary16 storage: rounding keys from the new time index, then array and element
+    uint32_t tkey = 0;
+    if constexpr (!std::is_same<T, TS>::value) tkey = hash32((uint32_t)(*(const volatile long long*)a.tdev + 1));
+    const uint32_t akey = tkey ^ 0x68e31da4u;
     __shared__ double s_part[kW][MP_MAX_SPECIES * (kMaxF - 1)];
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const int k = blk * kB + threadIdx.x;
@@ -363,7 +459,7 @@ __device__ __forceinline__ void step_body(const Args<T>& a, int blk, int nblk, c
             const uint32_t mask = __ldg(a.fmask + k);
             const Nbr b = node_nbrs(a, n);
             const Flow4<T> ur = a.u4[n];
-            const V xr = Pv[n];
+            const V xr = ld_wide<T, TS, FP>(Pv + n);
             const T whl_face = rn_mul(weight<T>(1), hl), whl_edge = rn_mul(weight<T>(5), hl);
             T delta[FP];
 #pragma unroll
@@ -374,7 +470,7 @@ __device__ __forceinline__ void step_body(const Args<T>& a, int blk, int nblk, c
                 if ((mask >> (i - 1)) & 1u) {
                     const int s = src_of(b, i);
                     const Flow4<T> uf = a.u4[s];
-                    const V xs = Pv[s];
+                    const V xs = ld_wide<T, TS, FP>(Pv + s);
                     const T whl = is_face(i) ? whl_face : whl_edge;
                     const T pin = rn_fma(weight<T>(i), qlink(edot<T>(i, uf.x, uf.y, uf.z), uf.w), whl);
                     const T pout = rn_fma(weight<T>(i), qlink(edot<T>(opposite(i), ur.x, ur.y, ur.z), ur.w), whl);
@@ -388,7 +484,7 @@ __device__ __forceinline__ void step_body(const Args<T>& a, int blk, int nblk, c
             }
             if (mask != kAllLinks) {
                 const int ai = iface_index(a, n);
-                const V xa = Av[ai];
+                const V xa = ld_wide<T, TS, FP>(Av + ai);
                 V xan;
 #pragma unroll
                 for (int f = 0; f < FP; ++f) {
@@ -396,12 +492,12 @@ __device__ __forceinline__ void step_body(const Args<T>& a, int blk, int nblk, c
                     delta[f] = rn_sub(delta[f], js);
                     xan.v[f] = rn_add(xa.v[f], js);
                 }
-                Anv[ai] = xan;
+                st_narrow<T, TS, FP>(Anv + ai, xan, akey + (uint32_t)ai * FP, a.stochastic);
             }
             V xn;
 #pragma unroll
             for (int f = 0; f < FP; ++f) xn.v[f] = rn_add(xr.v[f], delta[f]);
-            Pnv[n] = xn;
+            st_narrow<T, TS, FP>(Pnv + n, xn, tkey + (uint32_t)n * FP, a.stochastic);
 #pragma unroll
             for (int m = 0; m < kMaxF - 1; ++m)
                 if (m < a.M && 1 + m < FP) zv[m] = xn.v[(1 + m) < FP ? 1 + m : 0] * pick(us, a.dir[m]);
@@ -423,6 +519,7 @@ __device__ __forceinline__ void step_body(const Args<T>& a, int blk, int nblk, c
         constexpr int kCP = 2;
         constexpr int kMaxPass = MP_MAX_SPECIES / (kCP * kSC);
         using VC = FieldVec<T, kSC * FP>;
+        using VCS = FieldVec<TS, kSC * FP>;
         // per-species constants staged in shared memory, read with compile-time indices
         __shared__ T s_whf[MP_MAX_SPECIES], s_whe[MP_MAX_SPECIES], s_hl[MP_MAX_SPECIES], s_pa[MP_MAX_SPECIES],
             s_pd[MP_MAX_SPECIES];
@@ -434,10 +531,10 @@ __device__ __forceinline__ void step_body(const Args<T>& a, int blk, int nblk, c
             s_pd[j] = a.pd[j];
         }
         __syncthreads();
-        const VC* __restrict__ Pc = reinterpret_cast<const VC*>(P);
-        VC* __restrict__ Pnc = reinterpret_cast<VC*>(Pn);
-        const VC* __restrict__ Ac = reinterpret_cast<const VC*>(A);
-        VC* __restrict__ Anc = reinterpret_cast<VC*>(An);
+        const VCS* __restrict__ Pc = reinterpret_cast<const VCS*>(P);
+        VCS* __restrict__ Pnc = reinterpret_cast<VCS*>(Pn);
+        const VCS* __restrict__ Ac = reinterpret_cast<const VCS*>(A);
+        VCS* __restrict__ Anc = reinterpret_cast<VCS*>(An);
         const int cpn = a.SP / kSC;  // chunks per node
         int n = 0, aidx = 0;
         uint32_t mask = 0;
@@ -462,7 +559,7 @@ __device__ __forceinline__ void step_body(const Args<T>& a, int blk, int nblk, c
             if (active) {
 #pragma unroll
                 for (int cc = 0; cc < kCP; ++cc) {
-                    if (cc < nc) xr[cc] = ld_rec(Pc + (size_t)(c0 + cc) * a.N + n);
+                    if (cc < nc) xr[cc] = ld_wide<T, TS, kSC * FP>(Pc + (size_t)(c0 + cc) * a.N + n);
 #pragma unroll
                     for (int j = 0; j < kSC * FP; ++j) delta[cc][j] = T(0);
                 }
@@ -484,7 +581,7 @@ __device__ __forceinline__ void step_body(const Args<T>& a, int blk, int nblk, c
 #pragma unroll
                         for (int cc = 0; cc < kCP; ++cc) {
                             if (cc < nc) {
-                                const VC xs = ld_rec(Pc + (size_t)(c0 + cc) * a.N + s);
+                                const VC xs = ld_wide<T, TS, kSC * FP>(Pc + (size_t)(c0 + cc) * a.N + s);
 #pragma unroll
                                 for (int q = 0; q < kSC; ++q) {
                                     const int sp = (c0 + cc) * kSC + q;
@@ -514,7 +611,7 @@ __device__ __forceinline__ void step_body(const Args<T>& a, int blk, int nblk, c
                 if (active && cc < nc) {
                     if (mask != kAllLinks) {
                         const size_t ai = (size_t)(c0 + cc) * a.NI + aidx;
-                        const VC xa = ld_rec(Ac + ai);
+                        const VC xa = ld_wide<T, TS, kSC * FP>(Ac + ai);
                         VC xan;
 #pragma unroll
                         for (int q = 0; q < kSC; ++q) {
@@ -528,12 +625,13 @@ __device__ __forceinline__ void step_body(const Args<T>& a, int blk, int nblk, c
                                 xan.v[j] = rn_add(xa.v[j], js);
                             }
                         }
-                        st_rec(Anc + ai, xan);
+                        st_narrow<T, TS, kSC * FP>(Anc + ai, xan, akey + (uint32_t)ai * (kSC * FP), a.stochastic);
                     }
                     VC xn;
 #pragma unroll
                     for (int j = 0; j < kSC * FP; ++j) xn.v[j] = rn_add(xr[cc].v[j], delta[cc][j]);
-                    st_rec(Pnc + (size_t)(c0 + cc) * a.N + n, xn);
+                    const size_t pi = (size_t)(c0 + cc) * a.N + n;
+                    st_narrow<T, TS, kSC * FP>(Pnc + pi, xn, tkey + (uint32_t)pi * (kSC * FP), a.stochastic);
 #pragma unroll
                     for (int q = 0; q < kSC; ++q) {
                         const T h = s_hl[(c0 + cc) * kSC + q];
@@ -577,8 +675,9 @@ __device__ __forceinline__ void step_body(const Args<T>& a, int blk, int nblk, c
     // s_t1 is only read by thread 0 of the last block, after the barriers in grid_total
     bool last = grid_total<kB>(a.partials, K, a.ticket, nblk, [&](int kk, double tot) {
         const long long t1 = s_t1;
-        Z[(size_t)kk * cap + t1] = tot;
-        D[(size_t)kk * cap + t1] = D[(size_t)kk * cap + t1 - 1] + tot;
+        const double z = tot * a.zsc[kk / a.M];  // series kk = species * M + moment
+        Z[(size_t)kk * cap + t1] = z;
+        D[(size_t)kk * cap + t1] = D[(size_t)kk * cap + t1 - 1] + z;
     });
     if (last && threadIdx.x == 0) *tdev = s_t1;
 }
@@ -593,14 +692,14 @@ constexpr int min_blocks(bool single, int block, int elem)
     return elem == 8 ? 1 : (single ? 2048 / block : (768 / block > 1 ? 768 / block : 1));
 }
 
-template <typename T, int FP, bool kSingle>
+template <typename T, typename TS, int FP, bool kSingle>
 __global__ void __launch_bounds__(kThreads, min_blocks(kSingle, kThreads, sizeof(T)))
-    k_step(const __grid_constant__ Args<T> a, const T* __restrict__ P, T* __restrict__ Pn,
-           const T* __restrict__ A, T* __restrict__ An)
+    k_step(const __grid_constant__ Args<T> a, const TS* __restrict__ P, TS* __restrict__ Pn,
+           const TS* __restrict__ A, TS* __restrict__ An)
 {
     // __grid_constant__: step_body reads the arguments through a reference, straight from
     // the constant bank (without it the whole structure would be copied per thread)
-    step_body<T, FP, kSingle, kThreads>(a, blockIdx.x, gridDim.x, P, Pn, A, An);
+    step_body<T, TS, FP, kSingle, kThreads>(a, blockIdx.x, gridDim.x, P, Pn, A, An);
 }
 
 // ---------------------------------------------------------------------------------------
@@ -642,7 +741,7 @@ __global__ void __launch_bounds__(kB, kSingle ? 1536 / kB : min_blocks(false, kB
         }
     }
     const GroupPtrs p = g.ptrs[phase * g.n + c];
-    step_body<float, FP, kSingle, kB>(g.args[c], (int)blockIdx.x - b0, b1 - b0, p.P, p.Pn, p.A, p.An);
+    step_body<float, float, FP, kSingle, kB>(g.args[c], (int)blockIdx.x - b0, b1 - b0, p.P, p.Pn, p.A, p.An);
 }
 
 // ---------------------------------------------------------------------------------------
@@ -650,9 +749,9 @@ __global__ void __launch_bounds__(kB, kSingle ? 1536 / kB : min_blocks(false, kB
 // t = 1 (P_g(r,1) = sum_i pi(r - c_i) p_i(r - c_i) c_ig, no adsorbed share), Z_g(0), Z_g(1).
 // The free Boltzmann weight pi = 1/Z is the same on every fluid node (neutral tracer).
 // ---------------------------------------------------------------------------------------
-template <typename T>
+template <typename T, typename TS>
 __global__ void __launch_bounds__(kThreads)
-    k_init(const Args<T> a, const InitExtra b, T* __restrict__ P1, T* __restrict__ A1)
+    k_init(const Args<T> a, const InitExtra b, TS* __restrict__ P1, TS* __restrict__ A1)
 {
     const int k = blockIdx.x * kThreads + threadIdx.x;
     const bool active = k < a.NF;
@@ -662,6 +761,7 @@ __global__ void __launch_bounds__(kThreads)
     for (int sp = 0; sp < a.S; ++sp) {
         const T hl = a.hl[sp], pa = a.pa[sp], pd = a.pd[sp];
         const T invZ = (T)b.invZ[sp];
+        const T sc = (T)b.sc[sp];  // stored values are field values x sc
         T zp[2 * kMaxF] = {T(0), T(0), T(0), T(0), T(0), T(0), T(0), T(0)};
         if (active) {
             T pin[kQ], pout[kQ];
@@ -681,9 +781,9 @@ __global__ void __launch_bounds__(kThreads)
             if (d.itf) {
                 const size_t ai = elem(a, a.NI, d.aidx, sp, 0);
                 xn += pd * xa0;
-                A1[ai] = pa * x0 + (T(1) - pd) * xa0;
+                A1[ai] = Narrow<TS>::one((pa * x0 + (T(1) - pd) * xa0) * sc, 0u, false);
             }
-            P1[elem(a, a.N, d.n, sp, 0)] = xn;
+            P1[elem(a, a.N, d.n, sp, 0)] = Narrow<TS>::one(xn * sc, 0u, false);
 #pragma unroll
             for (int m = 0; m < kMaxF - 1; ++m) {
                 if (m < a.M) {
@@ -693,8 +793,8 @@ __global__ void __launch_bounds__(kThreads)
                     for (int i = 1; i < kQ; ++i)
                         if (ci(i, g) != 0) pg += pin[i] * T(ci(i, g));
                     pg *= invZ;
-                    P1[elem(a, a.N, d.n, sp, 1 + m)] = pg;
-                    if (d.itf) A1[elem(a, a.NI, d.aidx, sp, 1 + m)] = T(0);
+                    P1[elem(a, a.N, d.n, sp, 1 + m)] = Narrow<TS>::one(pg * sc, 0u, false);
+                    if (d.itf) A1[elem(a, a.NI, d.aidx, sp, 1 + m)] = Narrow<TS>::one(T(0), 0u, false);
                     T us, us2;
                     mean_step(pout, g, us, us2);
                     zp[2 * m] = invZ * us2;
@@ -747,19 +847,19 @@ __global__ void __launch_bounds__(kThreads)
 
 // FP64 per-block partial sums of the density field of one species: sum_F P, sum_I Gamma,
 // sum_I P.
-template <typename T>
+template <typename T, typename TS>
 __global__ void __launch_bounds__(kThreads)
-    k_mass(const Args<T> a, int sp, const T* __restrict__ P, const T* __restrict__ A, double* __restrict__ out)
+    k_mass(const Args<T> a, int sp, const TS* __restrict__ P, const TS* __restrict__ A, double* __restrict__ out)
 {
     const int k = blockIdx.x * kThreads + threadIdx.x;
     double v[3] = {0.0, 0.0, 0.0};
     if (k < a.NF) {
         const int n = __ldg(a.flist + k);
-        v[0] = (double)P[elem(a, a.N, n, sp, 0)];
+        v[0] = (double)widen1(P[elem(a, a.N, n, sp, 0)]);
         const uint32_t bits = __ldg(a.iface + (n >> 5));
         if ((bits >> (n & 31)) & 1u) {
             const int j = __ldg(a.ibase + (n >> 5)) + __popc(bits & ((1u << (n & 31)) - 1u));
-            v[1] = (double)A[elem(a, a.NI, j, sp, 0)];
+            v[1] = (double)widen1(A[elem(a, a.NI, j, sp, 0)]);
             v[2] = v[0];
         }
     }
@@ -847,6 +947,8 @@ struct mp_ctx {
     int SP = 1;  // species padded to whole chunks (1 for one species)
     int SC = 1;  // species per chunk
     mp_group* owner = nullptr;  // set while the context steps as part of a group
+    double zsc[MP_MAX_SPECIES] = {};  // stored value x zsc = field value (binary16 storage)
+    int stochastic = 1;               // binary16 rounding: stochastic (1) or to nearest (0)
     // runs of kCtxGraphSteps steps captured once per starting buffer (cur) and replayed
     cudaGraph_t graph[2] = {nullptr, nullptr};
     cudaGraphExec_t exec[2] = {nullptr, nullptr};
@@ -886,6 +988,8 @@ Args<T> make_args(const mp_ctx* c)
         a.pa[s] = (T)c->ka[s];
         a.pd[s] = (T)c->kd[s];
     }
+    for (int s = 0; s < c->S; ++s) a.zsc[s] = c->zsc[s];
+    a.stochastic = c->stochastic;
     a.partials = c->partials;
     a.ticket = c->ticket;
     a.Z = c->Z;
@@ -917,9 +1021,17 @@ void destroy(mp_ctx* c)
     delete c;
 }
 
-template <typename T>
+template <typename T, typename TS>
 int init_typed(mp_ctx* c, const float* u_in, int init_density)
 {
+    // binary16 storage keeps field values x Z_s (the partition function), so the
+    // equilibrium free density is stored as 1; other storage types are unscaled
+    double invZ[MP_MAX_SPECIES];
+    for (int s = 0; s < c->S; ++s) {
+        const double K = c->ka[s] == 0.0 ? 0.0 : c->ka[s] / c->kd[s];
+        invZ[s] = 1.0 / ((double)c->geo.n_fluid + K * (double)c->geo.n_iface);
+        c->zsc[s] = std::is_same<T, TS>::value ? 1.0 : invZ[s];
+    }
     const int N = c->geo.N;
     const size_t NI = (size_t)(c->geo.n_iface > 0 ? c->geo.n_iface : 1);
     c->FP = c->F <= 2 ? 2 : 4;
@@ -929,15 +1041,15 @@ int init_typed(mp_ctx* c, const float* u_in, int init_density)
     const size_t fieldN = (size_t)c->SP * N * c->FP;
     const size_t fieldA = (size_t)c->SP * NI * c->FP;
     const int Kser = c->S * c->M;
-    c->elem = sizeof(T);
+    c->elem = sizeof(TS);
     c->blocks = (int)((c->geo.n_fluid + kThreads - 1) / kThreads);
     MP_CUDA(cudaMalloc(&c->u4, sizeof(Flow4<T>) * (size_t)N));
     MP_CUDA(cudaMalloc(&c->fmask, sizeof(uint32_t) * (size_t)c->geo.n_fluid));
     for (int b = 0; b < 2; ++b) {
-        MP_CUDA(cudaMalloc(&c->P[b], sizeof(T) * fieldN));
-        MP_CUDA(cudaMalloc(&c->A[b], sizeof(T) * fieldA));
-        MP_CUDA(cudaMemsetAsync(c->P[b], 0, sizeof(T) * fieldN, c->stream));
-        MP_CUDA(cudaMemsetAsync(c->A[b], 0, sizeof(T) * fieldA, c->stream));
+        MP_CUDA(cudaMalloc(&c->P[b], sizeof(TS) * fieldN));
+        MP_CUDA(cudaMalloc(&c->A[b], sizeof(TS) * fieldA));
+        MP_CUDA(cudaMemsetAsync(c->P[b], 0, sizeof(TS) * fieldN, c->stream));
+        MP_CUDA(cudaMemsetAsync(c->A[b], 0, sizeof(TS) * fieldA, c->stream));
     }
     MP_CUDA(cudaMalloc(&c->Z, sizeof(double) * (size_t)Kser * c->cap));
     MP_CUDA(cudaMalloc(&c->D, sizeof(double) * (size_t)Kser * c->cap));
@@ -979,13 +1091,13 @@ int init_typed(mp_ctx* c, const float* u_in, int init_density)
     InitExtra b;
     memset(&b, 0, sizeof(b));
     for (int s = 0; s < c->S; ++s) {
-        double K = c->ka[s] == 0.0 ? 0.0 : c->ka[s] / c->kd[s];
-        b.K[s] = K;
-        b.invZ[s] = 1.0 / ((double)c->geo.n_fluid + K * (double)c->geo.n_iface);
+        b.K[s] = c->ka[s] == 0.0 ? 0.0 : c->ka[s] / c->kd[s];
+        b.invZ[s] = invZ[s];
+        b.sc[s] = 1.0 / c->zsc[s];
     }
     b.inv_nf = 1.0 / (double)c->geo.n_fluid;
     b.uniform = init_density == MP_INIT_UNIFORM;
-    k_init<T><<<c->blocks, kThreads, 0, c->stream>>>(a, b, (T*)c->P[0], (T*)c->A[0]);
+    k_init<T, TS><<<c->blocks, kThreads, 0, c->stream>>>(a, b, (TS*)c->P[0], (TS*)c->A[0]);
     MP_CUDA(cudaGetLastError());
     c->cur = 0;
     c->t = 1;
@@ -1001,17 +1113,17 @@ bool capturable(cudaStream_t s)
     return s != nullptr && s != cudaStreamLegacy && s != cudaStreamPerThread;
 }
 
-template <typename T>
+template <typename T, typename TS>
 int step_typed(mp_ctx* c, long long n)
 {
     Args<T> a = make_args<T>(c);
-    auto kern = c->FP == 2 ? (c->S == 1 ? k_step<T, 2, true> : k_step<T, 2, false>)
-                           : (c->S == 1 ? k_step<T, 4, true> : k_step<T, 4, false>);
+    auto kern = c->FP == 2 ? (c->S == 1 ? k_step<T, TS, 2, true> : k_step<T, TS, 2, false>)
+                           : (c->S == 1 ? k_step<T, TS, 4, true> : k_step<T, TS, 4, false>);
     auto launch = [&](long long count) {
         for (long long k = 0; k < count; ++k) {
             const int s = c->cur;
-            kern<<<c->blocks, kThreads, 0, c->stream>>>(a, (const T*)c->P[s], (T*)c->P[1 - s], (const T*)c->A[s],
-                                                        (T*)c->A[1 - s]);
+            kern<<<c->blocks, kThreads, 0, c->stream>>>(a, (const TS*)c->P[s], (TS*)c->P[1 - s], (const TS*)c->A[s],
+                                                        (TS*)c->A[1 - s]);
             c->cur = 1 - s;
         }
     };
@@ -1038,13 +1150,13 @@ int step_typed(mp_ctx* c, long long n)
     return MP_OK;
 }
 
-template <typename T>
+template <typename T, typename TS>
 int mass_typed(mp_ctx* c, int sp, double out[3])
 {
     Args<T> a = make_args<T>(c);
-    const T* P = (const T*)c->P[c->cur];
-    const T* A = (const T*)c->A[c->cur];
-    k_mass<T><<<c->blocks, kThreads, 0, c->stream>>>(a, sp, P, A, c->partials);
+    const TS* P = (const TS*)c->P[c->cur];
+    const TS* A = (const TS*)c->A[c->cur];
+    k_mass<T, TS><<<c->blocks, kThreads, 0, c->stream>>>(a, sp, P, A, c->partials);
     std::vector<double> h((size_t)c->blocks * 3);
     MP_CUDA(cudaGetLastError());
     MP_CUDA(cudaMemcpyAsync(h.data(), c->partials, h.size() * sizeof(double), cudaMemcpyDeviceToHost, c->stream));
@@ -1052,6 +1164,7 @@ int mass_typed(mp_ctx* c, int sp, double out[3])
     out[0] = out[1] = out[2] = 0.0;
     for (int b = 0; b < c->blocks; ++b)
         for (int j = 0; j < 3; ++j) out[j] += h[(size_t)b * 3 + j];
+    for (int j = 0; j < 3; ++j) out[j] *= c->zsc[sp];
     return MP_OK;
 }
 
@@ -1078,6 +1191,7 @@ void mp_default_options(mp_options* opt)
     opt->allow_negative = 0;
     opt->capacity = 131072;
     opt->stream = nullptr;
+    opt->rounding = MP_ROUND_STOCHASTIC;
 }
 
 const char* mp_last_error(void) { return mp::last_error_text(); }
@@ -1099,8 +1213,12 @@ int mp_init_batch(mp_ctx** out, const mp_geometry* g, const float* u, int n_spec
         set_error("n_species must be in 1..MP_MAX_SPECIES with non-NULL parameter arrays");
         return MP_EINVAL;
     }
-    if (opt.precision != MP_FP32 && opt.precision != MP_FP64) {
-        set_error("precision must be MP_FP32 or MP_FP64");
+    if (opt.precision != MP_FP32 && opt.precision != MP_FP64 && opt.precision != MP_FP16) {
+        set_error("precision must be MP_FP32, MP_FP64 or MP_FP16");
+        return MP_EINVAL;
+    }
+    if (opt.rounding != MP_ROUND_STOCHASTIC && opt.rounding != MP_ROUND_NEAREST) {
+        set_error("rounding must be MP_ROUND_STOCHASTIC or MP_ROUND_NEAREST");
         return MP_EINVAL;
     }
     if (opt.directions < 1 || opt.directions > 7) {
@@ -1128,6 +1246,10 @@ int mp_init_batch(mp_ctx** out, const mp_geometry* g, const float* u, int n_spec
             set_error("k_a > 0 with k_d = 0 has no equilibrium (Boltzmann weights need K = k_a/k_d)");
             return MP_EINVAL;
         }
+        if (opt.precision == MP_FP16 && k_a[s] > 30000.0 * k_d[s]) {
+            set_error("binary16 storage needs K = k_a/k_d <= 30000 (stored adsorbed values reach K)");
+            return MP_EINVAL;
+        }
     }
     mp_ctx* c = new (std::nothrow) mp_ctx();
     if (!c) {
@@ -1135,6 +1257,7 @@ int mp_init_batch(mp_ctx** out, const mp_geometry* g, const float* u, int n_spec
         return MP_ENOMEM;
     }
     c->precision = opt.precision;
+    c->stochastic = opt.rounding == MP_ROUND_STOCHASTIC;
     c->stream = (cudaStream_t)opt.stream;
     c->cap = opt.capacity;
     c->S = n_species;
@@ -1168,7 +1291,9 @@ int mp_init_batch(mp_ctx** out, const mp_geometry* g, const float* u, int n_spec
             return rc;
         }
     }
-    rc = c->precision == MP_FP64 ? init_typed<double>(c, u, opt.init_density) : init_typed<float>(c, u, opt.init_density);
+    rc = c->precision == MP_FP64   ? init_typed<double, double>(c, u, opt.init_density)
+         : c->precision == MP_FP16 ? init_typed<float, __half>(c, u, opt.init_density)
+                                   : init_typed<float, float>(c, u, opt.init_density);
     if (rc == MP_OK && c->n_neg_links > 0 && !opt.allow_negative) {
         set_error(std::to_string(c->n_neg_links) +
                   " open links have a negative probability p_i (set allow_negative to accept)");
@@ -1204,7 +1329,9 @@ int mp_step(mp_ctx* c, int64_t n)
         set_error("the context belongs to a group: step it with mp_group_step");
         return MP_EINVAL;
     }
-    return c->precision == MP_FP64 ? step_typed<double>(c, n) : step_typed<float>(c, n);
+    return c->precision == MP_FP64   ? step_typed<double, double>(c, n)
+           : c->precision == MP_FP16 ? step_typed<float, __half>(c, n)
+                                     : step_typed<float, float>(c, n);
 }
 
 int mp_vacf(mp_ctx* c, int species, int direction, double* Z, double* D, int64_t cap, int64_t* n_out)
@@ -1236,7 +1363,9 @@ int mp_mass(mp_ctx* c, int species, double out[3])
         set_error("species out of range or out is NULL");
         return MP_EINVAL;
     }
-    return c->precision == MP_FP64 ? mass_typed<double>(c, species, out) : mass_typed<float>(c, species, out);
+    return c->precision == MP_FP64   ? mass_typed<double, double>(c, species, out)
+           : c->precision == MP_FP16 ? mass_typed<float, __half>(c, species, out)
+                                     : mass_typed<float, float>(c, species, out);
 }
 
 int mp_info(mp_ctx* c, mp_info_t* info)
@@ -1274,10 +1403,13 @@ int mp_get_field(mp_ctx* c, int species, int field, double* free_dense, double* 
     MP_CUDA(cudaMemcpyAsync(abuf.data(), c->A[c->cur], abuf.size(), cudaMemcpyDeviceToHost, c->stream));
     MP_CUDA(cudaStreamSynchronize(c->stream));
     const size_t SC = (size_t)c->SC;
+    const double zsc = c->zsc[species];
     auto at = [&](const std::vector<char>& v, size_t i) {
         const size_t rows = &v == &buf ? N : NI;
         const size_t j = ((((size_t)species / SC) * rows + i) * SC + (size_t)species % SC) * FP + (size_t)field;
-        return E == 8 ? ((const double*)v.data())[j] : (double)((const float*)v.data())[j];
+        if (E == 8) return ((const double*)v.data())[j];
+        if (E == 4) return (double)((const float*)v.data())[j];
+        return (double)__half2float(((const __half*)v.data())[j]) * zsc;
     };
     for (size_t n = 0; n < N; ++n) free_dense[n] = at(buf, n);
     if (ads_dense) {
@@ -1306,13 +1438,16 @@ int mp_set_field(mp_ctx* c, int species, int field, const double* free_dense, co
     MP_CUDA(cudaMemcpyAsync(abuf.data(), c->A[c->cur], abuf.size(), cudaMemcpyDeviceToHost, c->stream));
     MP_CUDA(cudaStreamSynchronize(c->stream));
     const size_t SC = (size_t)c->SC;
+    const double zsc = c->zsc[species];
     auto put = [&](std::vector<char>& v, size_t i, double x) {
         const size_t rows = &v == &buf ? N : NI;
         const size_t j = ((((size_t)species / SC) * rows + i) * SC + (size_t)species % SC) * FP + (size_t)field;
         if (E == 8)
             ((double*)v.data())[j] = x;
-        else
+        else if (E == 4)
             ((float*)v.data())[j] = (float)x;
+        else
+            ((__half*)v.data())[j] = __float2half_rn((float)(x / zsc));
     };
     for (size_t n = 0; n < N; ++n) put(buf, n, ((fl[n >> 5] >> (n & 31)) & 1u) ? free_dense[n] : 0.0);
     for (size_t k = 0; k < c->ilist.size(); ++k) put(abuf, k, ads_dense ? ads_dense[c->ilist[k]] : 0.0);

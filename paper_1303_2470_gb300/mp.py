@@ -31,6 +31,9 @@ MP_HOST = 0
 MP_DEVICE = 1
 MP_FP32 = 0
 MP_FP64 = 1
+MP_FP16 = 2
+MP_ROUND_STOCHASTIC = 0
+MP_ROUND_NEAREST = 1
 MP_INIT_EQUILIBRIUM = 0
 MP_INIT_UNIFORM = 1
 MP_MAX_SPECIES = 32
@@ -44,7 +47,7 @@ class mp_geometry(ctypes.Structure):
 
 class mp_options(ctypes.Structure):
     _fields_ = [("precision", _c_int), ("directions", _c_int), ("init_density", _c_int),
-                ("allow_negative", _c_int), ("capacity", _c_i64), ("stream", _c_vp)]
+                ("allow_negative", _c_int), ("capacity", _c_i64), ("stream", _c_vp), ("rounding", _c_int)]
 
 
 class mp_info_t(ctypes.Structure):
@@ -139,9 +142,10 @@ def mp_default_options() -> mp_options:
 
 
 def _options(precision="fp32", directions="x", init_density="equilibrium", allow_negative=False,
-             capacity=0, stream=None):
+             capacity=0, stream=None, rounding="stochastic"):
     o = mp_default_options()
-    o.precision = {"fp32": MP_FP32, "fp64": MP_FP64}[precision]
+    o.precision = {"fp32": MP_FP32, "fp64": MP_FP64, "fp16": MP_FP16}[precision]
+    o.rounding = {"stochastic": MP_ROUND_STOCHASTIC, "nearest": MP_ROUND_NEAREST}[rounding]
     o.directions = sum({"x": 1, "y": 2, "z": 4}[d] for d in directions)
     o.init_density = {"equilibrium": MP_INIT_EQUILIBRIUM, "uniform": MP_INIT_UNIFORM}[init_density]
     o.allow_negative = int(bool(allow_negative))
@@ -172,7 +176,8 @@ class Context:
 
 def mp_init(solid, u, D_b, k_a, k_d, **options) -> Context:
     """mp_init of include/mp.h. solid: host numpy or device tensor (nz,ny,nx) uint8;
-    u: device FP32 buffer of 3*N values (SoA) or None. Options: precision ("fp32"/"fp64"),
+    u: device FP32 buffer of 3*N values (SoA) or None. Options: precision ("fp32"/"fp64"/"fp16"),
+    rounding of fp16 storage ("stochastic"/"nearest"),
     directions (e.g. "x", "xz"), init_density ("equilibrium"/"uniform"), allow_negative,
     capacity, stream."""
     return mp_init_batch(solid, u, [D_b], [k_a], [k_d], **options)
