@@ -286,6 +286,79 @@ def run_batched(args):
     return 0
 
 
+def run_surrogate(args):
+    """LB warm start from the trained surrogate against the cold start (both to residual
+    1e-7, checked every 10 steps, at the force giving the benchmark's mean interstitial
+    velocity 0.01): unseen 64^3 media, the benchmark's 128^3 medium and unseen 256^3 media. Reports steps and wall time (the warm time includes the network's inference),
+    the estimate's error, the distance between the two converged flows and, on the benchmark
+    medium, the largest relative difference of D(t) over 2000 MP steps run on either flow."""
+    import torch
+    from paper_1303_2470_gb300 import build, media
+    build.build()
+    from paper_1303_2470_gb300 import mp, surrogate
+    model, meta = surrogate.load()
+    rng = np.random.default_rng(77)
+    cases = [("unseen 64^3", 64, int(rng.integers(4, 9)), float(rng.uniform(0.3, 0.6)), 90_001 + i) for i in range(8)]
+    cases += [("benchmark medium 128^3", 128, WORKLOAD["radius"], WORKLOAD["porosity"], WORKLOAD["seed"])]
+    cases += [("unseen 256^3", 256, 6, 0.40, 90_101), ("unseen 256^3", 256, 5, 0.50, 90_102)]
+    out = []
+    check = 10
+    for label, n, R, phi, seed in cases:
+        solid, _ = media.random_spheres((n, n, n), R, phi, seed)
+        sd = torch.as_tensor(solid).cuda()
+        fl = sd == 0
+        # operating force: the benchmark's mean interstitial velocity 0.01 (Stokes-linear
+        # rescaling of a calibration solve, which is not timed)
+        u_cold = torch.zeros((3, n, n, n), dtype=torch.float32, device="cuda")
+        mp.lb_steady(sd, (1e-5, 0.0, 0.0), u_cold, tol=1e-7, max_steps=200_000, check_every=100)
+        force = (1e-5 * WORKLOAD["mean_u"] / float(u_cold[0][fl].double().mean()), 0.0, 0.0)
+        u_cold.zero_()
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        n_cold, _, c_cold = mp.lb_steady(sd, force, u_cold, tol=1e-7, max_steps=200_000, check_every=check)
+        torch.cuda.synchronize()
+        t_cold = time.perf_counter() - t0
+        t0 = time.perf_counter()
+        u0, rho0 = surrogate.warm_start(solid, force, model)
+        torch.cuda.synchronize()
+        t_inf = time.perf_counter() - t0
+        u_warm = torch.zeros_like(u_cold)
+        n_warm, _, c_warm = mp.lb_steady(sd, force, u_warm, tol=1e-7, max_steps=200_000, check_every=check,
+                                         u_init=u0, rho_init=rho0)
+        torch.cuda.synchronize()
+        t_warm = time.perf_counter() - t0
+        rec = {"case": label, "n": n, "radius": R, "porosity": round(phi, 4), "seed": seed, "force_x": force[0],
+               "check_every": check, "cold_steps": int(n_cold), "warm_steps": int(n_warm),
+               "converged": bool(c_cold and c_warm),
+               "cold_s": round(t_cold, 4), "warm_s": round(t_warm, 4), "inference_s": round(t_inf, 4),
+               "estimate_rel_l2": float((u0 - u_cold).norm() / u_cold.norm()),
+               "flow_max_rel_diff": float((u_warm - u_cold).abs().max() / u_cold.abs().max())}
+        if label.startswith("benchmark"):
+            # the downstream observable: D(t) of the benchmark's tracer on either flow
+            Ds = []
+            for u in (u_cold, u_warm):
+                ctx = mp.mp_init(sd, u, WORKLOAD["D_b"], WORKLOAD["k_a"], WORKLOAD["k_d"], capacity=2002,
+                                 allow_negative=True)
+                mp.mp_step(ctx, 2000)
+                Ds.append(mp.mp_vacf(ctx, 0, 0)[1])
+                ctx.close()
+            rec["D_max_rel_diff"] = float(np.max(np.abs(Ds[1] / Ds[0] - 1.0)))
+        out.append(rec)
+        print(json.dumps(rec), flush=True)
+        del u_cold, u_warm, u0, rho0, sd
+    line = {"metric": "LB steps to residual 1e-7: cold start / surrogate warm start", "unit": "ratio",
+            "steps_factor": {c: float(np.mean([r["cold_steps"] / r["warm_steps"] for r in out if r["case"] == c]))
+                             for c in dict.fromkeys(r["case"] for r in out)},
+            "time_factor": {c: float(np.mean([r["cold_s"] / r["warm_s"] for r in out if r["case"] == c]))
+                            for c in dict.fromkeys(r["case"] for r in out)},
+            "cases": out,
+            "model": {"n_params": meta["n_params"], "train_media": meta["n_train"], "size": meta["size"],
+                      "iters": meta["iters"], "batch": meta["batch"], "train_seconds": meta["train_seconds"],
+                      "final_loss": meta["loss_history"][-1][1]}}
+    print(json.dumps(line))
+    return 0
+
+
 def run_profile_batched():
     """Two random-sphere media (96^3, 128^3) x 16 species, 30 LB steps each, then 8 grouped
     steps without graph or autotune: `k_step_group` launches for ncu captures."""
@@ -339,9 +412,10 @@ def main():
     ap.add_argument("--precision", default="fp32", choices=["fp32", "fp16"],
                     help="field storage of the MP step: fp32 (default) or binary16 with FP32 "
                          "arithmetic and stochastic rounding")
-    ap.add_argument("--workload", default="porous128", choices=["porous128", "batched"],
+    ap.add_argument("--workload", default="porous128", choices=["porous128", "batched", "surrogate"],
                     help="porous128: the single-species 128^3 job (the bench line); batched: three "
-                         "media x 16 species, grouped launch vs one species per launch")
+                         "media x 16 species, grouped launch vs one species per launch; surrogate: LB "
+                         "steps to steady from the learned warm start vs the cold start")
     ap.add_argument("--profile-batched", action="store_true",
                     help="short grouped run (96^3 and 128^3 media x 16 species) for ncu captures")
     ap.add_argument("--profile", action="store_true",
@@ -357,6 +431,8 @@ def main():
         return run_profile_batched()
     if args.workload == "batched":
         return run_batched(args)
+    if args.workload == "surrogate":
+        return run_surrogate(args)
 
     import torch
     import torch.distributed as dist

@@ -294,9 +294,13 @@ const char* mp_last_error(void);
  *                max_steps) the populations are replaced by the mean of the last two
  *                iterates: this keeps the fixed point and removes the undamped period-2
  *                modes that bounce-back sustains at nodes with few open links.
- *  u_init        device, FP32 3*N, or NULL: start from f^eq(rho = 1, u_init) (cold start
- *                from rest when NULL).
+ *  u_init        device, FP32 3*N, or NULL (rest): starting velocity;
+ *  rho_init      device, FP32 N, or NULL (1 everywhere): starting density. The start is
+ *                f^eq(rho_init, u_init); NULL, NULL is the cold start from rest. The mass of
+ *                every connected fluid region is conserved from the start, so a warm start
+ *                reaches the cold start's steady state only with the same mass per region.
  *  u_out         device, FP32 3*N: u at the final step, zero on solid nodes.
+ *  rho_out       device, FP32 N, or NULL: the density at the final step (0 on solids).
  *  steps_out, residual_out   host (either may be NULL): steps taken, last residual.
  *  stream        cudaStream_t or NULL. Allocates its working populations stream-ordered
  *                and frees them before returning; synchronises the stream.
@@ -304,8 +308,8 @@ const char* mp_last_error(void);
  * and residual_out are still written), MP_EINVAL, MP_ENOMEM or MP_ECUDA.
  */
 int lb_steady(const mp_geometry* g, const double force[3], double tau, double tol,
-              int64_t max_steps, int64_t check_every, const float* u_init, float* u_out,
-              int64_t* steps_out, double* residual_out, void* stream);
+              int64_t max_steps, int64_t check_every, const float* u_init, const float* rho_init,
+              float* u_out, float* rho_out, int64_t* steps_out, double* residual_out, void* stream);
 
 #ifdef __cplusplus
 }

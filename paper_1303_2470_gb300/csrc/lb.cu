@@ -41,18 +41,22 @@ __device__ __forceinline__ bool lb_bit(const uint32_t* __restrict__ w, int n)
 }
 __device__ __forceinline__ int lb_wrap(int v, int n) { return v < 0 ? v + n : (v >= n ? v - n : v); }
 
-// mode 0: plain step; 1: also store u into u_prev; 2: store u into u_out, fold
-// max|u - u_prev| (FP64) into *res_bits (non-negative doubles order like their bits), then
-// store u into u_prev.
+// mode 0: plain step; 1: also store u into u_prev; 2: store u into u_out (and rho into
+// rho_out when given), fold max|u - u_prev| (FP64) into *res_bits (non-negative doubles
+// order like their bits), then store u into u_prev.
 __global__ void __launch_bounds__(kLbThreads)
     k_lb_step(const LbArgs a, const float* __restrict__ g, float* __restrict__ gn, int mode,
-              float* __restrict__ u_prev, float* __restrict__ u_out, unsigned long long* __restrict__ res_bits)
+              float* __restrict__ u_prev, float* __restrict__ u_out, float* __restrict__ rho_out,
+              unsigned long long* __restrict__ res_bits)
 {
     const int n = blockIdx.x * kLbThreads + threadIdx.x;
     double res = 0.0;
     if (n < a.N) {
         if (!lb_bit(a.fluid, n)) {
-            if (mode == 2) u_out[n] = u_out[a.N + n] = u_out[2 * a.N + n] = 0.0f;
+            if (mode == 2) {
+                u_out[n] = u_out[a.N + n] = u_out[2 * a.N + n] = 0.0f;
+                if (rho_out) rho_out[n] = 0.0f;
+            }
         } else {
             const int x = n % a.nx, y = (n / a.nx) % a.ny, z = n / (a.nx * a.ny);
             float f[kQ];
@@ -101,6 +105,7 @@ __global__ void __launch_bounds__(kLbThreads)
                 u_out[n] = ux;
                 u_out[a.N + n] = uy;
                 u_out[2 * a.N + n] = uz;
+                if (rho_out) rho_out[n] = rho;
                 res = fmax(fabs((double)ux - (double)u_prev[n]),
                            fmax(fabs((double)uy - (double)u_prev[a.N + n]), fabs((double)uz - (double)u_prev[2 * a.N + n])));
                 // this node's u(t) is the reference of the next check when it is due next step
@@ -124,23 +129,27 @@ __global__ void k_lb_mean(float* __restrict__ g0, const float* __restrict__ g1, 
         g0[k] = 0.5f * (g0[k] + g1[k]);
 }
 
-// f = f^eq(rho = 1, u0) (u0 = 0 when NULL) as deviations; u_prev = u0
-__global__ void k_lb_init(const LbArgs a, const float* __restrict__ u0, float* __restrict__ g, float* __restrict__ u_prev)
+// f = f^eq(rho0, u0) as deviations (u0 = 0 and rho0 = 1 when NULL); u_prev = u0
+__global__ void k_lb_init(const LbArgs a, const float* __restrict__ u0, const float* __restrict__ rho0,
+                          float* __restrict__ g, float* __restrict__ u_prev)
 {
     const int n = blockIdx.x * blockDim.x + threadIdx.x;
     if (n >= a.N) return;
     const bool fl = lb_bit(a.fluid, n);
-    float ux = 0.f, uy = 0.f, uz = 0.f;
+    float ux = 0.f, uy = 0.f, uz = 0.f, rho = 1.f;
     if (u0 && fl) {
         ux = u0[n];
         uy = u0[a.N + n];
         uz = u0[2 * a.N + n];
     }
+    if (rho0 && fl) rho = rho0[n];
     const float uu = ux * ux + uy * uy + uz * uz;
 #pragma unroll
     for (int i = 0; i < kQ; ++i) {
         const float cu = float(cx(i)) * ux + float(cy(i)) * uy + float(cz(i)) * uz;
-        g[(size_t)i * a.N + n] = fl ? weight<float>(i) * (3.0f * cu + 4.5f * cu * cu - 1.5f * uu) : 0.0f;
+        // f^eq - w = w [(rho - 1) + rho (3 cu + 4.5 cu^2 - 1.5 uu)]
+        g[(size_t)i * a.N + n] =
+            fl ? weight<float>(i) * ((rho - 1.0f) + rho * (3.0f * cu + 4.5f * cu * cu - 1.5f * uu)) : 0.0f;
     }
     u_prev[n] = ux;
     u_prev[a.N + n] = uy;
@@ -150,8 +159,8 @@ __global__ void k_lb_init(const LbArgs a, const float* __restrict__ u0, float* _
 }  // namespace
 
 extern "C" int lb_steady(const mp_geometry* geom, const double force[3], double tau, double tol, int64_t max_steps,
-                         int64_t check_every, const float* u_init, float* u_out, int64_t* steps_out,
-                         double* residual_out, void* stream_ptr)
+                         int64_t check_every, const float* u_init, const float* rho_init, float* u_out,
+                         float* rho_out, int64_t* steps_out, double* residual_out, void* stream_ptr)
 {
     clear_error();
     if (!force || !u_out || !(tau > 0.5) || max_steps < 1 || check_every < 1 || !(tol >= 0.0)) {
@@ -203,7 +212,7 @@ extern "C" int lb_steady(const mp_geometry* geom, const double force[3], double 
     a.inv_tau = (float)(1.0 / tau);
     a.guo = (float)(1.0 - 0.5 / tau);
     const int blocks = (G.N + kLbThreads - 1) / kLbThreads;
-    k_lb_init<<<blocks, kLbThreads, 0, s>>>(a, u_init, g0, uprev);
+    k_lb_init<<<blocks, kLbThreads, 0, s>>>(a, u_init, rho_init, g0, uprev);
     e = cudaGetLastError();
     int64_t t = 0;
     double res = INFINITY;
@@ -216,7 +225,7 @@ extern "C" int lb_steady(const mp_geometry* geom, const double force[3], double 
         else if ((t1 + 1) % check_every == 0 || t1 + 1 == max_steps)
             mode = 1;
         if (mode == 2) e = cudaMemsetAsync(res_d, 0, sizeof(unsigned long long), s);
-        k_lb_step<<<blocks, kLbThreads, 0, s>>>(a, g0, g1, mode, uprev, u_out, res_d);
+        k_lb_step<<<blocks, kLbThreads, 0, s>>>(a, g0, g1, mode, uprev, u_out, rho_out, res_d);
         if (e == cudaSuccess) e = cudaGetLastError();
         float* tmp = g0;
         g0 = g1;

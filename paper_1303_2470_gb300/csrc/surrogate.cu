@@ -1,0 +1,654 @@
+// surrogate.cu -- kernels of the learned warm start for lb_steady (include/surrogate.h): 3x3x3
+// periodic convolutions as implicit GEMMs on the tensor cores (mma.sync m16n8k16, BF16
+// operands, FP32 accumulation), their input and weight gradients, pooling, upsampling,
+// the masked loss and the Adam update. Nothing here belongs to the moment-propagation
+// method itself; the network's output only seeds lb_steady.
+#include <cuda_bf16.h>
+
+#include "../../include/surrogate.h"
+#include "internal.cuh"
+
+using namespace mp;
+
+namespace {
+
+typedef __nv_bfloat16 bf16;
+
+constexpr int kTM = 64;     // GEMM tile rows (voxels, or input channels for the weight gradient)
+constexpr int kTN = 64;     // GEMM tile columns (output channels)
+constexpr int kTK = 16;     // reduction step (channels, or voxels for the weight gradient)
+constexpr int kLd = 24;     // shared-memory row length in BF16 (48 bytes: conflict-free fragments)
+constexpr int kConvThreads = 128;
+
+__device__ __forceinline__ int wrap(int v, int n) { return v < 0 ? v + n : (v >= n ? v - n : v); }
+
+// D += A B for one m16n8k16 tile; fragments as the PTX ISA lays them out for .bf16:
+// a0..a3 rows (g, g+8) x cols (2t, 2t+1) and (+8); b0, b1 rows (2t, 2t+1) and (+8) of col g.
+__device__ __forceinline__ void mma16816(float (&d)[4], uint32_t a0, uint32_t a1, uint32_t a2, uint32_t a3,
+                                         uint32_t b0, uint32_t b1)
+{
+    asm volatile(
+        "mma.sync.aligned.m16n8k16.row.col.f32.bf16.bf16.f32 {%0,%1,%2,%3}, {%4,%5,%6,%7}, {%8,%9}, "
+        "{%0,%1,%2,%3};"
+        : "+f"(d[0]), "+f"(d[1]), "+f"(d[2]), "+f"(d[3])
+        : "r"(a0), "r"(a1), "r"(a2), "r"(a3), "r"(b0), "r"(b1));
+}
+
+__device__ __forceinline__ uint32_t lds32(const bf16* p) { return *reinterpret_cast<const uint32_t*>(p); }
+
+// one K step of a 64 x 64 tile: warp w owns rows 16w..16w+15, all 8 column tiles of 8
+__device__ __forceinline__ void tile_mma(const bf16 (*As)[kLd], const bf16 (*Bs)[kLd], float (&acc)[8][4], int ncols)
+{
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int g = lane >> 2, t = lane & 3, m = warp * 16;
+    const uint32_t a0 = lds32(&As[m + g][2 * t]), a1 = lds32(&As[m + g + 8][2 * t]);
+    const uint32_t a2 = lds32(&As[m + g][2 * t + 8]), a3 = lds32(&As[m + g + 8][2 * t + 8]);
+#pragma unroll
+    for (int nt = 0; nt < 8; ++nt) {
+        if (nt * 8 < ncols) {
+            const uint32_t b0 = lds32(&Bs[nt * 8 + g][2 * t]), b1 = lds32(&Bs[nt * 8 + g][2 * t + 8]);
+            mma16816(acc[nt], a0, a1, a2, a3, b0, b1);
+        }
+    }
+}
+
+struct ConvArgs {
+    const bf16* x;
+    const bf16* w;
+    const float* bias;
+    bf16* y;
+    float* yf;
+    int D, H, W, V, K, N, sign, relu;
+};
+
+// Implicit GEMM: rows = voxels of one sample (blockIdx.z), columns = output channels, the
+// reduction runs over the 27 taps and the input channels in steps of 16. Each thread stages
+// one 16-byte piece of the A tile (a voxel's 8 channels at the shifted position) and one of
+// the B tile (8 input channels of one output channel of the tap).
+__global__ void __launch_bounds__(kConvThreads) k_conv(const ConvArgs a)
+{
+    __shared__ __align__(16) bf16 As[kTM][kLd];
+    __shared__ __align__(16) bf16 Bs[kTN][kLd];
+    const int tid = threadIdx.x;
+    const int v0 = blockIdx.x * kTM, n0 = blockIdx.y * kTN, b = blockIdx.z;
+    const int ar = tid >> 1, ah = (tid & 1) * 8;
+    const int va = v0 + ar;
+    const bool vok = va < a.V;
+    int xa = 0, ya = 0, za = 0;
+    if (vok) {
+        xa = va % a.W;
+        ya = (va / a.W) % a.H;
+        za = va / (a.W * a.H);
+    }
+    const bool nok = n0 + ar < a.N;
+    const bf16* xb = a.x + (size_t)b * a.V * a.K;
+    const int ncols = a.N - n0 < kTN ? a.N - n0 : kTN;
+    float acc[8][4];
+#pragma unroll
+    for (int i = 0; i < 8; ++i) acc[i][0] = acc[i][1] = acc[i][2] = acc[i][3] = 0.0f;
+    for (int tap = 0; tap < 27; ++tap) {
+        const int dz = tap / 9 - 1, dy = (tap / 3) % 3 - 1, dx = tap % 3 - 1;
+        size_t src = 0;
+        if (vok) {
+            const int xs = wrap(xa + a.sign * dx, a.W), ys = wrap(ya + a.sign * dy, a.H), zs = wrap(za + a.sign * dz, a.D);
+            src = ((size_t)(zs * a.H + ys) * a.W + xs) * a.K;
+        }
+        const bf16* wt = a.w + ((size_t)tap * a.N + n0 + ar) * a.K;
+        for (int c0 = 0; c0 < a.K; c0 += kTK) {
+            uint4 av = make_uint4(0u, 0u, 0u, 0u), bv = make_uint4(0u, 0u, 0u, 0u);
+            if (vok) av = *reinterpret_cast<const uint4*>(xb + src + c0 + ah);
+            if (nok) bv = *reinterpret_cast<const uint4*>(wt + c0 + ah);
+            __syncthreads();
+            *reinterpret_cast<uint4*>(&As[ar][ah]) = av;
+            *reinterpret_cast<uint4*>(&Bs[ar][ah]) = bv;
+            __syncthreads();
+            tile_mma(As, Bs, acc, ncols);
+        }
+    }
+    const int lane = tid & 31, warp = tid >> 5, g = lane >> 2, t = lane & 3;
+#pragma unroll
+    for (int nt = 0; nt < 8; ++nt) {
+        const int col = n0 + nt * 8 + 2 * t;
+        if (col >= a.N) continue;
+        const float b0 = a.bias ? a.bias[col] : 0.0f, b1 = a.bias ? a.bias[col + 1] : 0.0f;
+#pragma unroll
+        for (int h = 0; h < 2; ++h) {
+            const int v = v0 + warp * 16 + g + 8 * h;
+            if (v >= a.V) continue;
+            float r0 = acc[nt][2 * h] + b0, r1 = acc[nt][2 * h + 1] + b1;
+            if (a.relu) {
+                r0 = fmaxf(r0, 0.0f);
+                r1 = fmaxf(r1, 0.0f);
+            }
+            const size_t o = ((size_t)b * a.V + v) * a.N + col;
+            if (a.y) *reinterpret_cast<__nv_bfloat162*>(a.y + o) = __floats2bfloat162_rn(r0, r1);
+            if (a.yf) {
+                a.yf[o] = r0;
+                a.yf[o + 1] = r1;
+            }
+        }
+    }
+}
+
+struct WgradArgs {
+    const bf16* x;
+    const bf16* dy;
+    float* dw;
+    int D, H, W, V, Cin, Cout;
+    long long total;  // B * V voxels of the reduction
+    int chunk;        // voxels per block
+};
+
+// Weight gradient of one tap (blockIdx.z % 27) over one chunk of voxels (blockIdx.z / 27):
+// rows = input channels, columns = output channels, reduction over voxels in steps of 16.
+// Thread (voxel kv = tid / 8, eight channels from 8 * (tid % 8)) stages one 16-byte piece of
+// x (at the shifted voxel) and of dy, transposed into the [channel][voxel] tiles.
+__global__ void __launch_bounds__(kConvThreads) k_wgrad(const WgradArgs a)
+{
+    __shared__ __align__(16) bf16 As[kTM][kLd];
+    __shared__ __align__(16) bf16 Bs[kTN][kLd];
+    const int tid = threadIdx.x;
+    const int tap = blockIdx.z % 27;
+    const long long e0 = (long long)(blockIdx.z / 27) * a.chunk;
+    const int ci0 = blockIdx.x * kTM, co0 = blockIdx.y * kTN;
+    const int dz = tap / 9 - 1, dy = (tap / 3) % 3 - 1, dx = tap % 3 - 1;
+    const int kv = tid >> 3, c8 = (tid & 7) * 8;
+    const int ncols = a.Cout - co0 < kTN ? a.Cout - co0 : kTN;
+    float acc[8][4];
+#pragma unroll
+    for (int i = 0; i < 8; ++i) acc[i][0] = acc[i][1] = acc[i][2] = acc[i][3] = 0.0f;
+    long long e1 = e0 + a.chunk;
+    if (e1 > a.total) e1 = a.total;
+    for (long long e = e0; e < e1; e += kTK) {
+        const long long ev = e + kv;
+        uint4 xv = make_uint4(0u, 0u, 0u, 0u), gv = make_uint4(0u, 0u, 0u, 0u);
+        if (ev < e1) {
+            const long long bb = ev / a.V;
+            const int v = (int)(ev - bb * a.V);
+            const int xa = v % a.W, ya = (v / a.W) % a.H, za = v / (a.W * a.H);
+            const int xs = wrap(xa + dx, a.W), ys = wrap(ya + dy, a.H), zs = wrap(za + dz, a.D);
+            const size_t src = (size_t)bb * a.V + (size_t)((zs * a.H + ys) * a.W + xs);
+            if (ci0 + c8 < a.Cin) xv = *reinterpret_cast<const uint4*>(a.x + src * a.Cin + ci0 + c8);
+            if (co0 + c8 < a.Cout) gv = *reinterpret_cast<const uint4*>(a.dy + (size_t)ev * a.Cout + co0 + c8);
+        }
+        __syncthreads();
+        const bf16* xp = reinterpret_cast<const bf16*>(&xv);
+        const bf16* gp = reinterpret_cast<const bf16*>(&gv);
+#pragma unroll
+        for (int j = 0; j < 8; ++j) {
+            As[c8 + j][kv] = xp[j];
+            Bs[c8 + j][kv] = gp[j];
+        }
+        __syncthreads();
+        tile_mma(As, Bs, acc, ncols);
+    }
+    const int lane = tid & 31, warp = tid >> 5, g = lane >> 2, t = lane & 3;
+#pragma unroll
+    for (int nt = 0; nt < 8; ++nt) {
+        const int co = co0 + nt * 8 + 2 * t;
+        if (co >= a.Cout) continue;
+#pragma unroll
+        for (int h = 0; h < 2; ++h) {
+            const int ci = ci0 + warp * 16 + g + 8 * h;
+            if (ci >= a.Cin) continue;
+            float* d = a.dw + ((size_t)tap * a.Cin + ci) * a.Cout + co;
+            atomicAdd(d, acc[nt][2 * h]);
+            atomicAdd(d + 1, acc[nt][2 * h + 1]);
+        }
+    }
+}
+
+// dbias[c] += sum over voxels of dy[.][c]: block = 256 voxels x one channel group of 32
+__global__ void k_bias_grad(const bf16* __restrict__ dy, float* __restrict__ db, long long total, int C)
+{
+    const int c = blockIdx.y * 32 + (threadIdx.x & 31);
+    const int r = threadIdx.x >> 5;  // 8 rows of voxels
+    float s = 0.0f;
+    if (c < C)
+        for (long long e = (long long)blockIdx.x * 256 + r; e < total && e < (long long)(blockIdx.x + 1) * 256; e += 8)
+            s += __bfloat162float(dy[(size_t)e * C + c]);
+    __shared__ float part[8][32];
+    part[r][threadIdx.x & 31] = s;
+    __syncthreads();
+    if (r == 0 && c < C) {
+        float t = 0.0f;
+        for (int k = 0; k < 8; ++k) t += part[k][threadIdx.x];
+        atomicAdd(db + c, t);
+    }
+}
+
+// pooling / upsampling over one BF16 channel pair per thread
+__global__ void k_pool2(const bf16* __restrict__ x, bf16* __restrict__ y, int B, int D, int H, int W, int C)
+{
+    const int d = D / 2, h = H / 2, w = W / 2, C2 = C / 2;
+    const long long n = (long long)B * d * h * w * C2;
+    const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    const int c = (int)(i % C2) * 2;
+    long long r = i / C2;
+    const int xo = (int)(r % w), yo = (int)((r / w) % h), zo = (int)((r / ((long long)w * h)) % d);
+    const int b = (int)(r / ((long long)w * h * d));
+    float s0 = 0.0f, s1 = 0.0f;
+    for (int k = 0; k < 8; ++k) {
+        const int xs = 2 * xo + (k & 1), ys = 2 * yo + ((k >> 1) & 1), zs = 2 * zo + (k >> 2);
+        const __nv_bfloat162 v = *reinterpret_cast<const __nv_bfloat162*>(
+            x + ((((size_t)b * D + zs) * H + ys) * W + xs) * C + c);
+        s0 += __low2float(v);
+        s1 += __high2float(v);
+    }
+    *reinterpret_cast<__nv_bfloat162*>(y + (size_t)r * C + c) = __floats2bfloat162_rn(s0 * 0.125f, s1 * 0.125f);
+}
+
+// fine-grid pass: every fine voxel reads its coarse parent (pool gradient / upsampling)
+template <bool kPoolGrad>
+__global__ void k_fine_from_coarse(const bf16* __restrict__ src, bf16* __restrict__ dst, int B, int D, int H, int W,
+                                   int C)
+{
+    // D, H, W: coarse sizes
+    const int Df = 2 * D, Hf = 2 * H, Wf = 2 * W, C2 = C / 2;
+    const long long n = (long long)B * Df * Hf * Wf * C2;
+    const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    const int c = (int)(i % C2) * 2;
+    const long long r = i / C2;
+    const int xf = (int)(r % Wf), yf = (int)((r / Wf) % Hf), zf = (int)((r / ((long long)Wf * Hf)) % Df);
+    const int b = (int)(r / ((long long)Wf * Hf * Df));
+    const size_t p = ((((size_t)b * D + zf / 2) * H + yf / 2) * W + xf / 2) * C + c;
+    __nv_bfloat162 v = *reinterpret_cast<const __nv_bfloat162*>(src + p);
+    if (kPoolGrad) v = __floats2bfloat162_rn(__low2float(v) * 0.125f, __high2float(v) * 0.125f);
+    *reinterpret_cast<__nv_bfloat162*>(dst + (size_t)r * C + c) = v;
+}
+
+// coarse-grid pass: sum of the 8 children (upsampling gradient)
+__global__ void k_up2_grad(const bf16* __restrict__ dy, bf16* __restrict__ dx, int B, int D, int H, int W, int C)
+{
+    const int C2 = C / 2;
+    const long long n = (long long)B * D * H * W * C2;
+    const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    const int c = (int)(i % C2) * 2;
+    const long long r = i / C2;
+    const int xo = (int)(r % W), yo = (int)((r / W) % H), zo = (int)((r / ((long long)W * H)) % D);
+    const int b = (int)(r / ((long long)W * H * D));
+    const int Hf = 2 * H, Wf = 2 * W, Df = 2 * D;
+    float s0 = 0.0f, s1 = 0.0f;
+    for (int k = 0; k < 8; ++k) {
+        const int xs = 2 * xo + (k & 1), ys = 2 * yo + ((k >> 1) & 1), zs = 2 * zo + (k >> 2);
+        const __nv_bfloat162 v = *reinterpret_cast<const __nv_bfloat162*>(
+            dy + ((((size_t)b * Df + zs) * Hf + ys) * Wf + xs) * C + c);
+        s0 += __low2float(v);
+        s1 += __high2float(v);
+    }
+    *reinterpret_cast<__nv_bfloat162*>(dx + (size_t)r * C + c) = __floats2bfloat162_rn(s0, s1);
+}
+
+__global__ void k_add(const bf16* __restrict__ a, const bf16* __restrict__ b, bf16* y, long long n)
+{
+    const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n) y[i] = __float2bfloat16_rn(__bfloat162float(a[i]) + __bfloat162float(b[i]));
+}
+
+__global__ void k_relu_grad(const bf16* __restrict__ act, bf16* __restrict__ g, long long n)
+{
+    const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n && !(__bfloat162float(act[i]) > 0.0f)) g[i] = __float2bfloat16_rn(0.0f);
+}
+
+// network coordinates (p, q, r) of lattice node (x, y, z) for a force along `axis`: the
+// forced axis comes first, the other two keep their order
+__device__ __forceinline__ void to_net(int axis, int x, int y, int z, int& p, int& q, int& r)
+{
+    if (axis == 0) {
+        p = x; q = y; r = z;
+    } else if (axis == 1) {
+        p = y; q = x; r = z;
+    } else {
+        p = z; q = x; r = y;
+    }
+}
+__device__ __forceinline__ void net_dims(int axis, int nx, int ny, int nz, int& P, int& Q, int& R)
+{
+    to_net(axis, nx, ny, nz, P, Q, R);
+}
+// lattice component of network channel c
+__device__ __forceinline__ int lattice_comp(int axis, int c)
+{
+    if (axis == 0) return c;
+    if (axis == 1) return c == 0 ? 1 : (c == 1 ? 0 : 2);
+    return c == 0 ? 2 : (c == 1 ? 0 : 1);
+}
+
+// network voxel index (x fastest in network order: p fastest) of lattice node n
+__device__ __forceinline__ int net_voxel(int axis, int n, int nx, int ny, int nz)
+{
+    const int x = n % nx, y = (n / nx) % ny, z = n / (nx * ny);
+    int p, q, r, P, Q, R;
+    to_net(axis, x, y, z, p, q, r);
+    net_dims(axis, nx, ny, nz, P, Q, R);
+    return (r * Q + q) * P + p;
+}
+
+__global__ void k_pack_input(const uint8_t* __restrict__ cls, bf16* __restrict__ x, int nx, int ny, int nz, int axis)
+{
+    const int n = blockIdx.x * blockDim.x + threadIdx.x;
+    const int N = nx * ny * nz;
+    if (n >= N) return;
+    const int v = net_voxel(axis, n, nx, ny, nz);
+    const uint8_t c = cls[n];
+    bf16* o = x + (size_t)v * 16;
+    const bf16 zero = __float2bfloat16_rn(0.0f);
+    o[0] = __float2bfloat16_rn((c & 3) != 0 ? 1.0f : 0.0f);
+    o[1] = __float2bfloat16_rn((c & 4) != 0 ? 1.0f : 0.0f);
+    for (int k = 2; k < 16; ++k) o[k] = zero;
+}
+
+// sum and count of y[.][3] over the forced cluster (FP64)
+__global__ void k_cluster_mean(const float* __restrict__ y, int ldy, const uint8_t* __restrict__ cls, int nx, int ny,
+                               int nz, int axis, double* __restrict__ acc)
+{
+    const int n = blockIdx.x * blockDim.x + threadIdx.x;
+    const int N = nx * ny * nz;
+    double s = 0.0, c = 0.0;
+    if (n < N && (cls[n] & 4)) {
+        s = y[(size_t)net_voxel(axis, n, nx, ny, nz) * ldy + 3];
+        c = 1.0;
+    }
+    for (int o = 16; o > 0; o >>= 1) {
+        s += __shfl_xor_sync(0xffffffffu, s, o);
+        c += __shfl_xor_sync(0xffffffffu, c, o);
+    }
+    if ((threadIdx.x & 31) == 0 && c > 0.0) {
+        atomicAdd(acc, s);
+        atomicAdd(acc + 1, c);
+    }
+}
+
+__global__ void k_unpack_output(const float* __restrict__ y, int ldy, const uint8_t* __restrict__ cls,
+                                float* __restrict__ u, float* __restrict__ rho, int nx, int ny, int nz, int axis,
+                                float scale_u, float scale_rho, const double* __restrict__ acc)
+{
+    const int n = blockIdx.x * blockDim.x + threadIdx.x;
+    const int N = nx * ny * nz;
+    if (n >= N || !(cls[n] & 4)) return;
+    const int v = net_voxel(axis, n, nx, ny, nz);
+    for (int c = 0; c < 3; ++c) u[(size_t)lattice_comp(axis, c) * N + n] += scale_u * y[(size_t)v * ldy + c];
+    if (rho) {
+        const float m = (float)(acc[0] / acc[1]);
+        rho[n] += scale_rho * (y[(size_t)v * ldy + 3] - m);
+    }
+}
+
+__global__ void k_pack_target(const float* __restrict__ u, const float* __restrict__ rho, float* __restrict__ t,
+                              int nx, int ny, int nz, int axis, float scale_u, float scale_rho)
+{
+    const int n = blockIdx.x * blockDim.x + threadIdx.x;
+    const int N = nx * ny * nz;
+    if (n >= N) return;
+    const int v = net_voxel(axis, n, nx, ny, nz);
+    for (int c = 0; c < 3; ++c) t[(size_t)v * 4 + c] = scale_u * u[(size_t)lattice_comp(axis, c) * N + n];
+    t[(size_t)v * 4 + 3] = rho[n] > 0.0f ? scale_rho * (rho[n] - 1.0f) : 0.0f;
+}
+
+__global__ void k_mse(const float* __restrict__ y, int ldy, const float* __restrict__ t, int nc,
+                      const bf16* __restrict__ x, bf16* __restrict__ dy, double* __restrict__ loss, long long total,
+                      double inv)
+{
+    const long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    double s = 0.0;
+    if (e < total) {
+        const bool fluid = __bfloat162float(x[(size_t)e * 16]) > 0.5f;
+        for (int c = 0; c < ldy; ++c) {
+            float gval = 0.0f;
+            if (fluid && c < nc) {
+                const float d = y[(size_t)e * ldy + c] - t[(size_t)e * nc + c];
+                s += (double)d * d;
+                gval = (float)(2.0 * inv) * d;
+            }
+            dy[(size_t)e * ldy + c] = __float2bfloat16_rn(gval);
+        }
+    }
+    for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+    if ((threadIdx.x & 31) == 0 && s != 0.0) atomicAdd(loss, s * inv);
+}
+
+__global__ void k_adam(float* __restrict__ p, const float* __restrict__ g, float* __restrict__ m, float* __restrict__ v,
+                       long long n, float lr, float b1, float b2, float eps, float c1, float c2, bf16* __restrict__ wf,
+                       bf16* __restrict__ wb, int cin, int cout)
+{
+    const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    const float gi = g[i];
+    const float mi = b1 * m[i] + (1.0f - b1) * gi;
+    const float vi = b2 * v[i] + (1.0f - b2) * gi * gi;
+    m[i] = mi;
+    v[i] = vi;
+    const float pi = p[i] - lr * (mi / c1) / (sqrtf(vi / c2) + eps);
+    p[i] = pi;
+    if (wf) {
+        // master index (tap, ci, co) -> forward copy [tap][co][ci], transposed copy [tap][ci][co]
+        const long long per = (long long)cin * cout;
+        const int tap = (int)(i / per);
+        const int ci = (int)((i % per) / cout), co = (int)(i % cout);
+        const bf16 h = __float2bfloat16_rn(pi);
+        wf[((size_t)tap * cout + co) * cin + ci] = h;
+        wb[i] = h;
+    }
+}
+
+int grid1(long long n, int block) { return (int)((n + block - 1) / block); }
+
+}  // namespace
+
+extern "C" {
+
+int sg_conv3d(const void* x, const void* w, const float* bias, void* y, float* yf, int B, int D, int H, int W, int K,
+              int N, int sign, int relu, void* stream)
+{
+    clear_error();
+    if (!x || !w || (!y && !yf) || B < 1 || D < 1 || H < 1 || W < 1 || K < 16 || N < 16 || K % 16 || N % 16 ||
+        (sign != 1 && sign != -1) || (long long)D * H * W > (1LL << 30)) {
+        set_error("sg_conv3d: needs x, w, an output, B, D, H, W >= 1, K and N multiples of 16, sign +-1");
+        return MP_EINVAL;
+    }
+    ConvArgs a{(const bf16*)x, (const bf16*)w, bias, (bf16*)y, yf, D, H, W, D * H * W, K, N, sign, relu != 0};
+    dim3 grid((a.V + kTM - 1) / kTM, (N + kTN - 1) / kTN, B);
+    k_conv<<<grid, kConvThreads, 0, (cudaStream_t)stream>>>(a);
+    MP_CUDA(cudaGetLastError());
+    return MP_OK;
+}
+
+int sg_conv3d_wgrad(const void* x, const void* dy, float* dw, float* dbias, int B, int D, int H, int W, int Cin,
+                    int Cout, void* stream)
+{
+    clear_error();
+    if (!x || !dy || !dw || B < 1 || D < 1 || H < 1 || W < 1 || Cin < 16 || Cout < 16 || Cin % 16 || Cout % 16) {
+        set_error("sg_conv3d_wgrad: needs x, dy, dw, positive sizes, Cin and Cout multiples of 16");
+        return MP_EINVAL;
+    }
+    WgradArgs a{(const bf16*)x, (const bf16*)dy, dw, D, H, W, D * H * W, Cin, Cout, (long long)B * D * H * W, 2048};
+    const long long nchunk = (a.total + a.chunk - 1) / a.chunk;
+    if (nchunk * 27 > 2147483647LL) {
+        set_error("sg_conv3d_wgrad: too many voxels");
+        return MP_EINVAL;
+    }
+    dim3 grid((Cin + kTM - 1) / kTM, (Cout + kTN - 1) / kTN, (unsigned)(nchunk * 27));
+    k_wgrad<<<grid, kConvThreads, 0, (cudaStream_t)stream>>>(a);
+    MP_CUDA(cudaGetLastError());
+    if (dbias) {
+        dim3 gb(grid1(a.total, 256), (Cout + 31) / 32);
+        k_bias_grad<<<gb, 256, 0, (cudaStream_t)stream>>>((const bf16*)dy, dbias, a.total, Cout);
+        MP_CUDA(cudaGetLastError());
+    }
+    return MP_OK;
+}
+
+int sg_pool2(const void* x, void* y, int B, int D, int H, int W, int C, void* stream)
+{
+    clear_error();
+    if (!x || !y || B < 1 || D < 2 || H < 2 || W < 2 || (D | H | W) & 1 || C < 2 || C & 1) {
+        set_error("sg_pool2: needs even D, H, W and an even channel count");
+        return MP_EINVAL;
+    }
+    const long long n = (long long)B * (D / 2) * (H / 2) * (W / 2) * (C / 2);
+    k_pool2<<<grid1(n, 256), 256, 0, (cudaStream_t)stream>>>((const bf16*)x, (bf16*)y, B, D, H, W, C);
+    MP_CUDA(cudaGetLastError());
+    return MP_OK;
+}
+
+int sg_pool2_grad(const void* dy, void* dx, int B, int D, int H, int W, int C, void* stream)
+{
+    clear_error();
+    if (!dy || !dx || B < 1 || D < 2 || H < 2 || W < 2 || (D | H | W) & 1 || C < 2 || C & 1) {
+        set_error("sg_pool2_grad: needs even D, H, W and an even channel count");
+        return MP_EINVAL;
+    }
+    const long long n = (long long)B * D * H * W * (C / 2);
+    k_fine_from_coarse<true><<<grid1(n, 256), 256, 0, (cudaStream_t)stream>>>((const bf16*)dy, (bf16*)dx, B, D / 2,
+                                                                               H / 2, W / 2, C);
+    MP_CUDA(cudaGetLastError());
+    return MP_OK;
+}
+
+int sg_up2(const void* x, void* y, int B, int D, int H, int W, int C, void* stream)
+{
+    clear_error();
+    if (!x || !y || B < 1 || D < 1 || H < 1 || W < 1 || C < 2 || C & 1) {
+        set_error("sg_up2: needs positive sizes and an even channel count");
+        return MP_EINVAL;
+    }
+    const long long n = (long long)B * 8 * D * H * W * (C / 2);
+    k_fine_from_coarse<false><<<grid1(n, 256), 256, 0, (cudaStream_t)stream>>>((const bf16*)x, (bf16*)y, B, D, H, W,
+                                                                                C);
+    MP_CUDA(cudaGetLastError());
+    return MP_OK;
+}
+
+int sg_up2_grad(const void* dy, void* dx, int B, int D, int H, int W, int C, void* stream)
+{
+    clear_error();
+    if (!dy || !dx || B < 1 || D < 1 || H < 1 || W < 1 || C < 2 || C & 1) {
+        set_error("sg_up2_grad: needs positive sizes and an even channel count");
+        return MP_EINVAL;
+    }
+    const long long n = (long long)B * D * H * W * (C / 2);
+    k_up2_grad<<<grid1(n, 256), 256, 0, (cudaStream_t)stream>>>((const bf16*)dy, (bf16*)dx, B, D, H, W, C);
+    MP_CUDA(cudaGetLastError());
+    return MP_OK;
+}
+
+int sg_add(const void* a, const void* b, void* y, int64_t n, void* stream)
+{
+    clear_error();
+    if (!a || !b || !y || n < 0) {
+        set_error("sg_add: NULL pointer or negative count");
+        return MP_EINVAL;
+    }
+    if (n == 0) return MP_OK;
+    k_add<<<grid1(n, 256), 256, 0, (cudaStream_t)stream>>>((const bf16*)a, (const bf16*)b, (bf16*)y, n);
+    MP_CUDA(cudaGetLastError());
+    return MP_OK;
+}
+
+int sg_relu_grad(const void* act, void* g, int64_t n, void* stream)
+{
+    clear_error();
+    if (!act || !g || n < 0) {
+        set_error("sg_relu_grad: NULL pointer or negative count");
+        return MP_EINVAL;
+    }
+    if (n == 0) return MP_OK;
+    k_relu_grad<<<grid1(n, 256), 256, 0, (cudaStream_t)stream>>>((const bf16*)act, (bf16*)g, n);
+    MP_CUDA(cudaGetLastError());
+    return MP_OK;
+}
+
+int sg_pack_input(const uint8_t* cls, void* x, int nx, int ny, int nz, int axis, void* stream)
+{
+    clear_error();
+    if (!cls || !x || nx < 1 || ny < 1 || nz < 1 || axis < 0 || axis > 2) {
+        set_error("sg_pack_input: bad arguments");
+        return MP_EINVAL;
+    }
+    const int N = nx * ny * nz;
+    k_pack_input<<<grid1(N, 256), 256, 0, (cudaStream_t)stream>>>(cls, (bf16*)x, nx, ny, nz, axis);
+    MP_CUDA(cudaGetLastError());
+    return MP_OK;
+}
+
+int sg_unpack_output(const float* y, int ldy, const uint8_t* cls, float* u, float* rho, int nx, int ny, int nz,
+                     int axis, float scale_u, float scale_rho, void* stream)
+{
+    clear_error();
+    if (!y || !cls || !u || ldy < (rho ? 4 : 3) || nx < 1 || ny < 1 || nz < 1 || axis < 0 || axis > 2) {
+        set_error("sg_unpack_output: bad arguments");
+        return MP_EINVAL;
+    }
+    cudaStream_t s = (cudaStream_t)stream;
+    const int N = nx * ny * nz;
+    double* acc = nullptr;
+    if (rho) {
+        MP_CUDA(cudaMallocAsync((void**)&acc, 2 * sizeof(double), s));
+        cudaError_t e = cudaMemsetAsync(acc, 0, 2 * sizeof(double), s);
+        if (e == cudaSuccess) {
+            k_cluster_mean<<<grid1(N, 256), 256, 0, s>>>(y, ldy, cls, nx, ny, nz, axis, acc);
+            e = cudaGetLastError();
+        }
+        if (e != cudaSuccess) {
+            cudaFreeAsync(acc, s);
+            return cuda_fail(e, "sg_unpack_output");
+        }
+    }
+    k_unpack_output<<<grid1(N, 256), 256, 0, s>>>(y, ldy, cls, u, rho, nx, ny, nz, axis, scale_u, scale_rho, acc);
+    cudaError_t e = cudaGetLastError();
+    if (acc) cudaFreeAsync(acc, s);
+    if (e != cudaSuccess) return cuda_fail(e, "sg_unpack_output");
+    return MP_OK;
+}
+
+int sg_pack_target(const float* u, const float* rho, float* t, int nx, int ny, int nz, int axis, float scale_u,
+                   float scale_rho, void* stream)
+{
+    clear_error();
+    if (!u || !rho || !t || nx < 1 || ny < 1 || nz < 1 || axis < 0 || axis > 2) {
+        set_error("sg_pack_target: bad arguments");
+        return MP_EINVAL;
+    }
+    const int N = nx * ny * nz;
+    k_pack_target<<<grid1(N, 256), 256, 0, (cudaStream_t)stream>>>(u, rho, t, nx, ny, nz, axis, scale_u, scale_rho);
+    MP_CUDA(cudaGetLastError());
+    return MP_OK;
+}
+
+int sg_mse(const float* y, int ldy, const float* t, int nc, const void* x, void* dy, double* loss, int B, int V,
+           double n_fluid, void* stream)
+{
+    clear_error();
+    if (!y || !t || !x || !dy || !loss || nc < 1 || nc > ldy || B < 1 || V < 1 || !(n_fluid > 0.0)) {
+        set_error("sg_mse: bad arguments");
+        return MP_EINVAL;
+    }
+    const long long total = (long long)B * V;
+    k_mse<<<grid1(total, 256), 256, 0, (cudaStream_t)stream>>>(y, ldy, t, nc, (const bf16*)x, (bf16*)dy, loss, total,
+                                                                1.0 / (nc * n_fluid));
+    MP_CUDA(cudaGetLastError());
+    return MP_OK;
+}
+
+int sg_adam(float* p, const float* g, float* m, float* v, int64_t n, float lr, float b1, float b2, float eps, int t,
+            void* wf, void* wb, int cin, int cout, void* stream)
+{
+    clear_error();
+    if (!p || !g || !m || !v || n < 0 || t < 1 || ((wf != nullptr) != (wb != nullptr)) ||
+        (wf && (cin < 1 || cout < 1 || n != 27LL * cin * cout))) {
+        set_error("sg_adam: bad arguments (weights need n = 27 cin cout and both copies)");
+        return MP_EINVAL;
+    }
+    if (n == 0) return MP_OK;
+    const float c1 = 1.0f - powf(b1, (float)t), c2 = 1.0f - powf(b2, (float)t);
+    k_adam<<<grid1(n, 256), 256, 0, (cudaStream_t)stream>>>(p, g, m, v, n, lr, b1, b2, eps, c1, c2, (bf16*)wf,
+                                                             (bf16*)wb, cin, cout);
+    MP_CUDA(cudaGetLastError());
+    return MP_OK;
+}
+
+}  // extern "C"

@@ -72,8 +72,8 @@ _lib.mp_get_field.argtypes = [_c_vp, _c_int, _c_int, _dp, _dp]
 _lib.mp_set_field.argtypes = [_c_vp, _c_int, _c_int, _dp, _dp]
 _lib.mp_free.argtypes = [_c_vp]
 _lib.mp_free.restype = None
-_lib.lb_steady.argtypes = [ctypes.POINTER(mp_geometry), _dp, _c_dbl, _c_dbl, _c_i64, _c_i64, _c_vp,
-                           _c_vp, ctypes.POINTER(_c_i64), _dp, _c_vp]
+_lib.lb_steady.argtypes = [ctypes.POINTER(mp_geometry), _dp, _c_dbl, _c_dbl, _c_i64, _c_i64, _c_vp, _c_vp,
+                           _c_vp, _c_vp, ctypes.POINTER(_c_i64), _dp, _c_vp]
 _lib.mp_classify.argtypes = [ctypes.POINTER(mp_geometry), _c_vp, ctypes.POINTER(_c_i64),
                              ctypes.POINTER(_c_i64), ctypes.POINTER(_c_i64), _c_vp]
 _lib.mp_step_noalloc.argtypes = [_c_int, _c_int, _c_int, _c_vp, _c_vp, _c_dbl, _c_dbl, _c_dbl, _c_int,
@@ -83,9 +83,23 @@ _lib.mp_group_step.argtypes = [_c_vp, _c_i64]
 _lib.mp_group_block_size.argtypes = [_c_vp]
 _lib.mp_group_free.argtypes = [_c_vp]
 _lib.mp_group_free.restype = None
+_f32, _c_i, _vp = ctypes.c_float, _c_int, _c_vp
+_lib.sg_conv3d.argtypes = [_vp, _vp, _vp, _vp, _vp] + [_c_i] * 8 + [_vp]
+_lib.sg_conv3d_wgrad.argtypes = [_vp, _vp, _vp, _vp] + [_c_i] * 6 + [_vp]
+for _f in ("sg_pool2", "sg_pool2_grad", "sg_up2", "sg_up2_grad"):
+    getattr(_lib, _f).argtypes = [_vp, _vp] + [_c_i] * 5 + [_vp]
+_lib.sg_add.argtypes = [_vp, _vp, _vp, _c_i64, _vp]
+_lib.sg_relu_grad.argtypes = [_vp, _vp, _c_i64, _vp]
+_lib.sg_pack_input.argtypes = [_vp, _vp, _c_i, _c_i, _c_i, _c_i, _vp]
+_lib.sg_unpack_output.argtypes = [_vp, _c_i, _vp, _vp, _vp, _c_i, _c_i, _c_i, _c_i, _f32, _f32, _vp]
+_lib.sg_pack_target.argtypes = [_vp, _vp, _vp, _c_i, _c_i, _c_i, _c_i, _f32, _f32, _vp]
+_lib.sg_mse.argtypes = [_vp, _c_i, _vp, _c_i, _vp, _vp, _vp, _c_i, _c_i, _c_dbl, _vp]
+_lib.sg_adam.argtypes = [_vp, _vp, _vp, _vp, _c_i64, _f32, _f32, _f32, _f32, _c_i, _vp, _vp, _c_i, _c_i, _vp]
 for _f in ("mp_init", "mp_init_batch", "mp_step", "mp_vacf", "mp_mass", "mp_info", "mp_get_field",
            "mp_set_field", "lb_steady", "mp_classify", "mp_step_noalloc", "mp_group_create",
-           "mp_group_step", "mp_group_block_size"):
+           "mp_group_step", "mp_group_block_size", "sg_conv3d", "sg_conv3d_wgrad", "sg_pool2",
+           "sg_pool2_grad", "sg_up2", "sg_up2_grad", "sg_add", "sg_relu_grad", "sg_pack_input",
+           "sg_unpack_output", "sg_pack_target", "sg_mse", "sg_adam"):
     getattr(_lib, _f).restype = _c_int
 
 
@@ -317,18 +331,79 @@ def mp_free(ctx: Context):
 
 
 def lb_steady(solid, force, u_out, tau=1.0, tol=1e-7, max_steps=1_000_000, check_every=100,
-              u_init=None, stream=None, raise_on_unconverged=False):
-    """lb_steady of include/mp.h; u_out (and u_init) are device FP32 buffers of 3*N values.
-    Returns (steps, residual, converged)."""
+              u_init=None, stream=None, raise_on_unconverged=False, rho_init=None, rho_out=None):
+    """lb_steady of include/mp.h; u_out (and u_init) are device FP32 buffers of 3*N values,
+    rho_init and rho_out of N values. Returns (steps, residual, converged)."""
     g, keep = make_geometry(solid)
     F = np.ascontiguousarray(force, dtype=np.float64)
     steps = _c_i64()
     res = _c_dbl()
     rc = _lib.lb_steady(ctypes.byref(g), F.ctypes.data_as(_dp), float(tau), float(tol), int(max_steps),
-                        int(check_every), _addr(u_init), _addr(u_out), ctypes.byref(steps),
+                        int(check_every), _addr(u_init), _addr(rho_init), _addr(u_out), _addr(rho_out),
+                        ctypes.byref(steps),
                         ctypes.byref(res), _stream(stream))
     del keep
     if rc == MP_ENOTCONVERGED and not raise_on_unconverged:
         return steps.value, res.value, False
     _check(rc)
     return steps.value, res.value, True
+
+
+# ---- kernels of the learned LB warm start (include/surrogate.h) ------------------------
+def sg_conv3d(x, w, bias, y, yf, B, D, H, W, K, N, sign=1, relu=False, stream=None):
+    _check(_lib.sg_conv3d(_addr(x), _addr(w), _addr(bias), _addr(y), _addr(yf), B, D, H, W, K, N, sign,
+                          int(bool(relu)), _stream(stream)))
+
+
+def sg_conv3d_wgrad(x, dy, dw, dbias, B, D, H, W, Cin, Cout, stream=None):
+    _check(_lib.sg_conv3d_wgrad(_addr(x), _addr(dy), _addr(dw), _addr(dbias), B, D, H, W, Cin, Cout,
+                                _stream(stream)))
+
+
+def sg_pool2(x, y, B, D, H, W, C, stream=None):
+    _check(_lib.sg_pool2(_addr(x), _addr(y), B, D, H, W, C, _stream(stream)))
+
+
+def sg_pool2_grad(dy, dx, B, D, H, W, C, stream=None):
+    _check(_lib.sg_pool2_grad(_addr(dy), _addr(dx), B, D, H, W, C, _stream(stream)))
+
+
+def sg_up2(x, y, B, D, H, W, C, stream=None):
+    _check(_lib.sg_up2(_addr(x), _addr(y), B, D, H, W, C, _stream(stream)))
+
+
+def sg_up2_grad(dy, dx, B, D, H, W, C, stream=None):
+    _check(_lib.sg_up2_grad(_addr(dy), _addr(dx), B, D, H, W, C, _stream(stream)))
+
+
+def sg_add(a, b, y, n, stream=None):
+    _check(_lib.sg_add(_addr(a), _addr(b), _addr(y), int(n), _stream(stream)))
+
+
+def sg_relu_grad(act, g, n, stream=None):
+    _check(_lib.sg_relu_grad(_addr(act), _addr(g), int(n), _stream(stream)))
+
+
+def sg_pack_input(cls, x, nx, ny, nz, axis, stream=None):
+    _check(_lib.sg_pack_input(_addr(cls), _addr(x), nx, ny, nz, axis, _stream(stream)))
+
+
+def sg_unpack_output(y, ldy, cls, u, rho, nx, ny, nz, axis, scale_u, scale_rho=0.0, stream=None):
+    _check(_lib.sg_unpack_output(_addr(y), ldy, _addr(cls), _addr(u), _addr(rho), nx, ny, nz, axis,
+                                 float(scale_u), float(scale_rho), _stream(stream)))
+
+
+def sg_pack_target(u, rho, t, nx, ny, nz, axis, scale_u, scale_rho, stream=None):
+    _check(_lib.sg_pack_target(_addr(u), _addr(rho), _addr(t), nx, ny, nz, axis, float(scale_u),
+                               float(scale_rho), _stream(stream)))
+
+
+def sg_mse(y, ldy, t, nc, x, dy, loss, B, V, n_fluid, stream=None):
+    _check(_lib.sg_mse(_addr(y), ldy, _addr(t), nc, _addr(x), _addr(dy), _addr(loss), B, V, float(n_fluid),
+                       _stream(stream)))
+
+
+def sg_adam(p, g, m, v, n, lr, b1, b2, eps, t, wf=None, wb=None, cin=0, cout=0, stream=None):
+    _check(_lib.sg_adam(_addr(p), _addr(g), _addr(m), _addr(v), int(n), float(lr), float(b1), float(b2),
+                        float(eps), int(t), _addr(wf), _addr(wb), cin, cout, _stream(stream)))
+

@@ -1,4 +1,4 @@
-"""The C-ABI library loads and exports every entry point include/mp.h declares (no GPU
+"""The C-ABI library loads and exports every entry point include/*.h declares (no GPU
 needed: nothing is called)."""
 import ctypes
 import os
@@ -10,7 +10,8 @@ ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
 
 
 def _declared():
-    src = open(os.path.join(ROOT, "include", "mp.h")).read()
+    import glob
+    src = "".join(open(h).read() for h in sorted(glob.glob(os.path.join(ROOT, "include", "*.h"))))
     src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
     names = re.findall(r"^\s*(?:const\s+)?[a-z_][a-z0-9_]*\s*\**\s+\**([a-z_][a-z0-9_]*)\s*\(",
                        src, flags=re.M)

@@ -1,0 +1,256 @@
+"""Kernels of the learned LB warm start (include/surrogate.h) against plain PyTorch FP32
+references of the same operations (CPU), and the warm start itself against the cold-start
+LB, which stays the judge.
+
+Tolerances follow from the arithmetic: operands are BF16 (the references get the same
+BF16-rounded values), products accumulate in FP32, and BF16 outputs carry a relative
+rounding of 2^-9; FP32 outputs and gradients differ from the reference only by summation
+order.
+"""
+import os
+
+import numpy as np
+import pytest
+
+from paper_1303_2470_gb300 import media
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+F = torch.nn.functional
+
+
+@pytest.fixture(scope="module")
+def mp():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_1303_2470_gb300 import build
+    build.build()
+    from paper_1303_2470_gb300 import mp as m
+    return m
+
+
+def _bf(a):
+    return torch.as_tensor(a, dtype=torch.float32).to(torch.bfloat16)
+
+
+def _ref_conv(x, w, bias, sign=1):
+    """x [B][D][H][W][K] fp32, w [27][N][K] -> y [B][D][H][W][N] with periodic padding."""
+    B, D, H, W, K = x.shape
+    N = w.shape[1]
+    wt = w.reshape(3, 3, 3, N, K).permute(3, 4, 0, 1, 2)          # [N][K][kz][ky][kx]
+    if sign < 0:
+        wt = torch.flip(wt, dims=(2, 3, 4))
+    xp = F.pad(x.permute(0, 4, 1, 2, 3), (1, 1, 1, 1, 1, 1), mode="circular")
+    y = F.conv3d(xp, wt, bias)
+    return y.permute(0, 2, 3, 4, 1)
+
+
+@pytest.mark.parametrize("shape,K,N,relu", [((2, 4, 8, 12), 32, 48, True), ((1, 6, 5, 7), 16, 16, False),
+                                            ((1, 8, 8, 8), 128, 64, True)])
+def test_conv_forward_matches_torch(mp, shape, K, N, relu):
+    B, D, H, W = shape
+    rng = np.random.default_rng(1)
+    x = _bf(rng.standard_normal((B, D, H, W, K)))
+    w = _bf(rng.standard_normal((27, N, K)) / np.sqrt(27 * K))
+    b = torch.as_tensor(rng.standard_normal(N), dtype=torch.float32)
+    ref = _ref_conv(x.float(), w.float(), b)
+    if relu:
+        ref = ref.clamp_min(0.0)
+    y = torch.empty((B, D * H * W, N), dtype=torch.bfloat16, device="cuda")
+    yf = torch.empty((B, D * H * W, N), dtype=torch.float32, device="cuda")
+    mp.sg_conv3d(x.cuda(), w.cuda(), b.cuda(), y, yf, B, D, H, W, K, N, 1, relu)
+    torch.cuda.synchronize()
+    ref = ref.reshape(B, D * H * W, N)
+    scale = float(ref.abs().max())
+    assert float((yf.cpu() - ref).abs().max()) <= 1e-5 * scale
+    assert float((y.float().cpu() - ref).abs().max()) <= 2.0 ** -8 * scale
+
+
+def test_conv_input_and_weight_gradients_match_autograd(mp):
+    B, D, H, W, K, N = 2, 4, 6, 8, 32, 48
+    rng = np.random.default_rng(2)
+    x = _bf(rng.standard_normal((B, D, H, W, K)))
+    wm = rng.standard_normal((27, K, N)) / np.sqrt(27 * K)          # master order [27][Cin][Cout]
+    wb = _bf(wm)
+    gy = _bf(rng.standard_normal((B, D, H, W, N)))
+    # autograd reference with the same BF16-valued operands
+    xr = x.float().requires_grad_(True)
+    wr = wb.float().permute(0, 2, 1).contiguous().requires_grad_(True)   # [27][N][K]
+    y = _ref_conv(xr, wr, None)
+    y.backward(gy.float())
+    gx_ref = xr.grad.reshape(B, D * H * W, K)
+    gw_ref = wr.grad.permute(0, 2, 1)                                      # [27][K][N]
+    gb_ref = gy.float().sum(dim=(0, 1, 2, 3))
+    # input gradient: transposed convolution with the master-order copy
+    gx = torch.empty((B, D * H * W, K), dtype=torch.float32, device="cuda")
+    mp.sg_conv3d(gy.cuda(), wb.cuda(), None, None, gx, B, D, H, W, N, K, -1, False)
+    gw = torch.zeros((27, K, N), dtype=torch.float32, device="cuda")
+    gbias = torch.zeros(N, dtype=torch.float32, device="cuda")
+    mp.sg_conv3d_wgrad(x.cuda(), gy.cuda(), gw, gbias, B, D, H, W, K, N)
+    torch.cuda.synchronize()
+    assert float((gx.cpu() - gx_ref).abs().max()) <= 1e-5 * float(gx_ref.abs().max())
+    assert float((gw.cpu() - gw_ref).abs().max()) <= 1e-5 * float(gw_ref.abs().max())
+    assert float((gbias.cpu() - gb_ref).abs().max()) <= 1e-5 * float(gb_ref.abs().max())
+
+
+def test_pool_up_add_relu_mse_adam(mp):
+    B, D, H, W, C = 2, 4, 6, 8, 32
+    rng = np.random.default_rng(3)
+    x = _bf(rng.standard_normal((B, D, H, W, C)))
+    xc = x.cuda()
+    p = torch.empty((B, D * H * W // 8, C), dtype=torch.bfloat16, device="cuda")
+    mp.sg_pool2(xc, p, B, D, H, W, C)
+    ref = F.avg_pool3d(x.float().permute(0, 4, 1, 2, 3), 2).permute(0, 2, 3, 4, 1).reshape(B, -1, C)
+    assert float((p.float().cpu() - ref).abs().max()) <= 2.0 ** -8 * float(ref.abs().max())
+    g = torch.empty_like(xc)
+    mp.sg_pool2_grad(p, g, B, D, H, W, C)
+    refg = torch.repeat_interleave(torch.repeat_interleave(torch.repeat_interleave(
+        p.float().cpu().reshape(B, D // 2, H // 2, W // 2, C), 2, 1), 2, 2), 2, 3) / 8
+    assert float((g.float().cpu() - refg).abs().max()) <= 2.0 ** -8 * float(refg.abs().max())
+    u = torch.empty((B, 8 * D * H * W, C), dtype=torch.bfloat16, device="cuda")
+    mp.sg_up2(xc, u, B, D, H, W, C)
+    refu = F.interpolate(x.float().permute(0, 4, 1, 2, 3), scale_factor=2, mode="nearest")
+    assert torch.equal(u.float().cpu(), refu.permute(0, 2, 3, 4, 1).reshape(B, -1, C))
+    gu = torch.empty_like(xc)
+    mp.sg_up2_grad(u, gu, B, D, H, W, C)
+    assert float((gu.float().cpu() - 8 * x.float()).abs().max()) <= 2.0 ** -8 * 8 * float(x.float().abs().max())
+    s = torch.empty_like(xc)
+    mp.sg_add(xc, xc, s, xc.numel())
+    assert torch.equal(s.float().cpu(), 2 * x.float())
+    gr = xc.clone()
+    mp.sg_relu_grad(xc, gr, gr.numel())
+    assert torch.equal(gr.float().cpu(), torch.where(x.float() > 0, x.float(), torch.zeros(())))
+    # masked MSE and its gradient
+    V = D * H * W
+    y = torch.as_tensor(rng.standard_normal((B, V, 16)), dtype=torch.float32).cuda()
+    t = torch.as_tensor(rng.standard_normal((B, V, 3)), dtype=torch.float32).cuda()
+    xin = torch.zeros((B, V, 16), dtype=torch.bfloat16, device="cuda")
+    fluid = torch.as_tensor(rng.random((B, V)) < 0.6)
+    xin[:, :, 0] = fluid.to(torch.bfloat16).cuda()
+    nf = float(fluid.sum())
+    loss = torch.zeros(1, dtype=torch.float64, device="cuda")
+    dy = torch.empty((B, V, 16), dtype=torch.bfloat16, device="cuda")
+    mp.sg_mse(y, 16, t, 3, xin, dy, loss, B, V, nf)
+    d = (y[:, :, :3] - t).cpu().double() * fluid[:, :, None]
+    assert abs(loss.item() - float((d ** 2).sum()) / (3 * nf)) <= 1e-12 * float((d ** 2).sum()) / (3 * nf)
+    refd = torch.zeros((B, V, 16), dtype=torch.float64)
+    refd[:, :, :3] = 2 * d / (3 * nf)
+    assert float((dy.float().cpu() - refd).abs().max()) <= 2.0 ** -8 * float(refd.abs().max())
+    # Adam, and the two BF16 weight copies
+    cin, cout = 16, 32
+    n = 27 * cin * cout
+    pm = torch.as_tensor(rng.standard_normal(n), dtype=torch.float32).cuda()
+    gm = torch.as_tensor(rng.standard_normal(n), dtype=torch.float32).cuda()
+    m, v = torch.zeros_like(pm), torch.zeros_like(pm)
+    wf = torch.empty((27, cout, cin), dtype=torch.bfloat16, device="cuda")
+    wbk = torch.empty((27, cin, cout), dtype=torch.bfloat16, device="cuda")
+    p0 = pm.cpu().double()
+    mp.sg_adam(pm, gm, m, v, n, 1e-2, 0.9, 0.999, 1e-8, 1, wf, wbk, cin, cout)
+    g0 = gm.cpu().double()
+    ref_p = p0 - 1e-2 * (0.1 * g0 / 0.1) / (torch.sqrt(0.001 * g0 ** 2 / 0.001) + 1e-8)
+    assert float((pm.cpu().double() - ref_p).abs().max()) <= 1e-6
+    assert torch.equal(wbk.cpu(), pm.cpu().to(torch.bfloat16).reshape(27, cin, cout))
+    assert torch.equal(wf.cpu(), pm.cpu().to(torch.bfloat16).reshape(27, cin, cout).permute(0, 2, 1))
+
+
+def _torch_net(params, x):
+    """The same network in PyTorch autograd (FP32, periodic padding); x [1][D][H][W][16]."""
+    def conv(name, h, relu=True):
+        W = params[name + ".W"]                                  # [27][cin][cout]
+        wt = W.reshape(3, 3, 3, W.shape[1], W.shape[2]).permute(4, 3, 0, 1, 2)
+        y = F.conv3d(F.pad(h, (1, 1, 1, 1, 1, 1), mode="circular"), wt, params[name + ".b"])
+        return y.clamp_min(0.0) if relu else y
+    h = x.permute(0, 4, 1, 2, 3)
+    s0 = conv("e0b", conv("e0a", h))
+    s1 = conv("e1b", conv("e1a", F.avg_pool3d(s0, 2)))
+    c2 = conv("b1", conv("b0", F.avg_pool3d(s1, 2)))
+    e1 = conv("d1b", conv("d1a", F.interpolate(c2, scale_factor=2)) + s1)
+    e0 = conv("d0b", conv("d0a", F.interpolate(e1, scale_factor=2)) + s0)
+    return conv("out", e0, relu=False).permute(0, 2, 3, 4, 1)
+
+
+def test_network_loss_and_gradients_match_autograd(mp):
+    """Forward, masked loss and every parameter gradient of the whole network on an 8^3 box
+    against PyTorch autograd of the same network with the same weights (BF16 activations and
+    gradients through eleven layers: outputs within 2 %, all gradients within 5 % in norm)."""
+    from paper_1303_2470_gb300 import surrogate
+    model = surrogate.Surrogate(seed=5)
+    for t in model.p.values():                                  # keep the FP32 masters exactly BF16
+        t["W"].copy_(t["W"].to(torch.bfloat16).float())
+        t["b"].normal_(0.0, 0.05)
+    model.adam(0.0, 1)                                          # refresh the BF16 copies
+    params = {k: torch.as_tensor(v) for k, v in model.state().items()}
+    solid, _ = media.random_spheres((8, 8, 8), 2, 0.55, seed=3)
+    cls, _ = mp.mp_classify(solid)
+    x0 = torch.empty((1, 512, 16), dtype=torch.bfloat16, device="cuda")
+    mp.sg_pack_input(torch.as_tensor(cls).cuda(), x0, 8, 8, 8, 0)
+    rng = np.random.default_rng(4)
+    tgt = torch.as_tensor(rng.standard_normal((1, 512, 3)), dtype=torch.float32).cuda()
+    y, acts = model.forward(x0, 1, (8, 8, 8), keep=True)
+    loss = torch.zeros(1, dtype=torch.float64, device="cuda")
+    gy = torch.empty((1, 512, 16), dtype=torch.bfloat16, device="cuda")
+    nf = float(x0[0, :, 0].float().sum())
+    mp.sg_mse(y, 16, tgt, 3, x0, gy, loss, 1, 512, nf)
+    model.zero_grad()
+    model.backward(acts, gy, 1, (8, 8, 8))
+    torch.cuda.synchronize()
+    # reference
+    pr = {k: v.clone().requires_grad_(True) for k, v in params.items()}
+    xr = x0.float().cpu().reshape(1, 8, 8, 8, 16)
+    yr = _torch_net(pr, xr).reshape(1, 512, 16)
+    fl = xr.reshape(1, 512, 16)[:, :, 0:1]
+    lr_ = (((yr[:, :, :3] - tgt.cpu()) ** 2) * fl).sum() / (3 * nf)
+    lr_.backward()
+    assert float((y.cpu() - yr.detach()).abs().max()) <= 2e-2 * float(yr.detach().abs().max())
+    assert abs(loss.item() / lr_.item() - 1.0) < 2e-2
+    # Each kernel is checked alone above (1e-5); this test checks the wiring (layer order,
+    # skips, pooling, ReLU masks), whose mistakes give errors of order one. Over all
+    # parameters the relative error is bounded by the BF16 stages: the deepest gradient passes
+    # 11 forward and 11 backward roundings of 2^-9, 22 x 2^-9 = 4.3 %, so 5 %. Per tensor the
+    # bound is looser (15 %): a bias gradient is a sum over voxels whose terms cancel, so its
+    # rounding error scales with the sum of their magnitudes, not with the sum itself.
+    num, den = 0.0, 0.0
+    for name, t in model.p.items():
+        for key in ("W", "b"):
+            ours = t["g" + key].cpu()
+            ref = pr[name + "." + key].grad
+            e = float((ours - ref).norm())
+            r = float(ref.norm())
+            assert e < 0.15 * r, (name, key, e / r)
+            num += e * e
+            den += r * r
+    assert np.sqrt(num / den) < 5e-2
+
+
+WEIGHTS = os.path.join(os.path.dirname(os.path.dirname(os.path.abspath(__file__))), "paper_1303_2470_gb300",
+                       "surrogate_weights.npz")
+
+
+@pytest.mark.skipif(not os.path.exists(WEIGHTS), reason="surrogate weights not trained")
+def test_warm_start_reaches_the_cold_start_flow_in_fewer_steps(mp):
+    """An unseen 64^3 medium (seed outside the training seeds), driven to a mean velocity of
+    about 0.01: lb_steady from the surrogate's estimate of (u, rho) converges to the same
+    residual 1e-7 and the same flow as from rest (the estimate's density has the cold
+    start's mass), in fewer steps (checked every 10 steps)."""
+    from paper_1303_2470_gb300 import surrogate
+    model, meta = surrogate.load()
+    solid, _ = media.random_spheres((64, 64, 64), 6, 0.45, seed=90_001)
+    sd = torch.as_tensor(solid).cuda()
+    u_cold = torch.zeros((3, 64, 64, 64), dtype=torch.float32, device="cuda")
+    mp.lb_steady(sd, (1e-5, 0.0, 0.0), u_cold, tol=1e-7, max_steps=100_000, check_every=100)
+    force = (1e-5 * 0.01 / float(u_cold[0][sd == 0].double().mean()), 0.0, 0.0)
+    u_cold.zero_()
+    n_cold, _, conv_cold = mp.lb_steady(sd, force, u_cold, tol=1e-7, max_steps=100_000, check_every=10)
+    u0, rho0 = surrogate.warm_start(solid, force, model)
+    cls, _ = mp.mp_classify(solid)
+    forced = torch.as_tensor(cls & 4 > 0).cuda()
+    assert abs(float(rho0[forced].double().mean()) - 1.0) < 1e-6     # same mass as the cold start
+    u_warm = torch.zeros_like(u_cold)
+    n_warm, _, conv_warm = mp.lb_steady(sd, force, u_warm, tol=1e-7, max_steps=100_000, check_every=10,
+                                        u_init=u0, rho_init=rho0)
+    assert conv_cold and conv_warm
+    scale = float(u_cold.abs().max())
+    assert float((u_warm - u_cold).abs().max()) <= 1e-3 * scale
+    est_err = float((u0 - u_cold).norm() / u_cold.norm())
+    print(f"\n64^3 unseen medium: cold {n_cold} steps, warm {n_warm} steps, estimate rel. L2 error {est_err:.3f}")
+    assert n_warm < n_cold
