@@ -5,9 +5,13 @@
 //   moments  rho = sum f_i, u = (sum f_i c_i + F/2) / rho;
 //   collide  f_i^post = f_i - (f_i - f_i^eq(rho,u))/tau
 //                       + (1 - 1/(2 tau)) w_i [3 (c_i - u) + 9 (c_i.u) c_i].F   (Guo force).
-// Populations are FP32 deviations g_i = f_i - w_i, structure of arrays g[i*N + n], which
-// keeps ~9 significant digits of the O(u) part that sets the velocity. Only fluid nodes
-// are read or written. The steady criterion max|u(t) - u(t-1)| is evaluated in FP64.
+// Populations are FP32 deviations g_i = f_i - w_i, which keeps ~9 significant digits of the
+// O(u) part that sets the velocity, stored for fluid nodes only, in the order of the sorted
+// fluid list: g[i*N_F + k] for fluid node k (structure of arrays). One thread per fluid node;
+// the compact index of a neighbour s is prefix[s >> 5] + popc(fluid bits of s's word below
+// s), from two bit-sized arrays that stay cache-resident, so a warp's reads and writes cover
+// whole sectors of fluid data only. The steady criterion max|u(t) - u(t-1)| is evaluated in
+// FP64.
 // The body force acts on the largest connected fluid cluster only (sealed pockets stay at
 // rest, their steady Stokes velocity). At every failed residual check the state is replaced
 // by the mean of the last two iterates: the fixed point is unchanged, an error mode of
@@ -27,8 +31,10 @@ namespace {
 constexpr int kLbThreads = 256;
 
 struct LbArgs {
-    int nx, ny, nz, N;
+    int nx, ny, nz, N, NF;
     const uint32_t* fluid;
+    const int32_t* fbase;    // fluid nodes before each 32-node word
+    const int32_t* flist;    // lattice node of fluid index k
     const uint32_t* forced;  // the force acts on these nodes (the largest fluid cluster)
     float Fx, Fy, Fz;
     float inv_tau;
@@ -43,76 +49,77 @@ __device__ __forceinline__ int lb_wrap(int v, int n) { return v < 0 ? v + n : (v
 
 // mode 0: plain step; 1: also store u into u_prev; 2: store u into u_out (and rho into
 // rho_out when given), fold max|u - u_prev| (FP64) into *res_bits (non-negative doubles
-// order like their bits), then store u into u_prev.
+// order like their bits), then store u into u_prev. u_prev is compact [3][N_F]; u_out and
+// rho_out are dense (their solid entries are zeroed once by the host).
 __global__ void __launch_bounds__(kLbThreads)
     k_lb_step(const LbArgs a, const float* __restrict__ g, float* __restrict__ gn, int mode,
               float* __restrict__ u_prev, float* __restrict__ u_out, float* __restrict__ rho_out,
               unsigned long long* __restrict__ res_bits)
 {
-    const int n = blockIdx.x * kLbThreads + threadIdx.x;
+    const int k = blockIdx.x * kLbThreads + threadIdx.x;
+    const size_t NF = (size_t)a.NF;
     double res = 0.0;
-    if (n < a.N) {
-        if (!lb_bit(a.fluid, n)) {
-            if (mode == 2) {
-                u_out[n] = u_out[a.N + n] = u_out[2 * a.N + n] = 0.0f;
-                if (rho_out) rho_out[n] = 0.0f;
-            }
-        } else {
-            const int x = n % a.nx, y = (n / a.nx) % a.ny, z = n / (a.nx * a.ny);
-            float f[kQ];
+    if (k < a.NF) {
+        const int n = __ldg(a.flist + k);
+        const int x = n % a.nx, y = (n / a.nx) % a.ny, z = n / (a.nx * a.ny);
+        float f[kQ];
 #pragma unroll
-            for (int i = 0; i < kQ; ++i) {
-                if (i == 0) {
-                    f[0] = g[n];
+        for (int i = 0; i < kQ; ++i) {
+            if (i == 0) {
+                f[0] = g[k];
+            } else {
+                const int s = lb_wrap(x - cx(i), a.nx) + a.nx * (lb_wrap(y - cy(i), a.ny) + a.ny * lb_wrap(z - cz(i), a.nz));
+                const uint32_t bits = __ldg(a.fluid + (s >> 5));
+                if ((bits >> (s & 31)) & 1u) {
+                    const int ks = __ldg(a.fbase + (s >> 5)) + __popc(bits & ((1u << (s & 31)) - 1u));
+                    f[i] = g[(size_t)i * NF + ks];
                 } else {
-                    const int s = lb_wrap(x - cx(i), a.nx) +
-                                  a.nx * (lb_wrap(y - cy(i), a.ny) + a.ny * lb_wrap(z - cz(i), a.nz));
-                    f[i] = lb_bit(a.fluid, s) ? g[(size_t)i * a.N + s] : g[(size_t)opposite(i) * a.N + n];
+                    f[i] = g[(size_t)opposite(i) * NF + k];  // halfway bounce-back
                 }
             }
-            float drho = 0.f, mx = 0.f, my = 0.f, mz = 0.f;
+        }
+        float drho = 0.f, mx = 0.f, my = 0.f, mz = 0.f;
 #pragma unroll
-            for (int i = 0; i < kQ; ++i) {
-                drho += f[i];
-                mx += float(cx(i)) * f[i];
-                my += float(cy(i)) * f[i];
-                mz += float(cz(i)) * f[i];
-            }
-            const bool on = lb_bit(a.forced, n);
-            const float Fx = on ? a.Fx : 0.0f, Fy = on ? a.Fy : 0.0f, Fz = on ? a.Fz : 0.0f;
-            const float rho = 1.0f + drho;
-            const float inv_rho = 1.0f / rho;
-            const float ux = (mx + 0.5f * Fx) * inv_rho;
-            const float uy = (my + 0.5f * Fy) * inv_rho;
-            const float uz = (mz + 0.5f * Fz) * inv_rho;
-            const float uu = ux * ux + uy * uy + uz * uz;
-            const float uF = ux * Fx + uy * Fy + uz * Fz;
+        for (int i = 0; i < kQ; ++i) {
+            drho += f[i];
+            mx += float(cx(i)) * f[i];
+            my += float(cy(i)) * f[i];
+            mz += float(cz(i)) * f[i];
+        }
+        const bool on = lb_bit(a.forced, n);
+        const float Fx = on ? a.Fx : 0.0f, Fy = on ? a.Fy : 0.0f, Fz = on ? a.Fz : 0.0f;
+        const float rho = 1.0f + drho;
+        const float inv_rho = 1.0f / rho;
+        const float ux = (mx + 0.5f * Fx) * inv_rho;
+        const float uy = (my + 0.5f * Fy) * inv_rho;
+        const float uz = (mz + 0.5f * Fz) * inv_rho;
+        const float uu = ux * ux + uy * uy + uz * uz;
+        const float uF = ux * Fx + uy * Fy + uz * Fz;
 #pragma unroll
-            for (int i = 0; i < kQ; ++i) {
-                const float w = weight<float>(i);
-                const float cu = float(cx(i)) * ux + float(cy(i)) * uy + float(cz(i)) * uz;
-                const float cF = float(cx(i)) * Fx + float(cy(i)) * Fy + float(cz(i)) * Fz;
-                // f^eq - w = w [(rho - 1) + rho (3 cu + 4.5 cu^2 - 1.5 uu)]
-                const float geq = w * (drho + rho * (3.0f * cu + 4.5f * cu * cu - 1.5f * uu));
-                const float src = a.guo * w * (3.0f * (cF - uF) + 9.0f * cu * cF);
-                gn[(size_t)i * a.N + n] = f[i] - a.inv_tau * (f[i] - geq) + src;
-            }
-            if (mode == 1) {
-                u_prev[n] = ux;
-                u_prev[a.N + n] = uy;
-                u_prev[2 * a.N + n] = uz;
-            } else if (mode == 2) {
-                u_out[n] = ux;
-                u_out[a.N + n] = uy;
-                u_out[2 * a.N + n] = uz;
-                if (rho_out) rho_out[n] = rho;
-                res = fmax(fabs((double)ux - (double)u_prev[n]),
-                           fmax(fabs((double)uy - (double)u_prev[a.N + n]), fabs((double)uz - (double)u_prev[2 * a.N + n])));
-                // this node's u(t) is the reference of the next check when it is due next step
-                u_prev[n] = ux;
-                u_prev[a.N + n] = uy;
-                u_prev[2 * a.N + n] = uz;
-            }
+        for (int i = 0; i < kQ; ++i) {
+            const float w = weight<float>(i);
+            const float cu = float(cx(i)) * ux + float(cy(i)) * uy + float(cz(i)) * uz;
+            const float cF = float(cx(i)) * Fx + float(cy(i)) * Fy + float(cz(i)) * Fz;
+            // f^eq - w = w [(rho - 1) + rho (3 cu + 4.5 cu^2 - 1.5 uu)]
+            const float geq = w * (drho + rho * (3.0f * cu + 4.5f * cu * cu - 1.5f * uu));
+            const float src = a.guo * w * (3.0f * (cF - uF) + 9.0f * cu * cF);
+            gn[(size_t)i * NF + k] = f[i] - a.inv_tau * (f[i] - geq) + src;
+        }
+        if (mode == 1) {
+            u_prev[k] = ux;
+            u_prev[NF + k] = uy;
+            u_prev[2 * NF + k] = uz;
+        } else if (mode == 2) {
+            u_out[n] = ux;
+            u_out[a.N + n] = uy;
+            u_out[2 * a.N + n] = uz;
+            if (rho_out) rho_out[n] = rho;
+            res = fmax(fabs((double)ux - (double)u_prev[k]),
+                       fmax(fabs((double)uy - (double)u_prev[NF + k]), fabs((double)uz - (double)u_prev[2 * NF + k])));
+            // this node's u(t) is the reference of the next check when it is due next step
+            u_prev[k] = ux;
+            u_prev[NF + k] = uy;
+            u_prev[2 * NF + k] = uz;
         }
     }
     if (mode == 2) {
@@ -129,31 +136,31 @@ __global__ void k_lb_mean(float* __restrict__ g0, const float* __restrict__ g1, 
         g0[k] = 0.5f * (g0[k] + g1[k]);
 }
 
-// f = f^eq(rho0, u0) as deviations (u0 = 0 and rho0 = 1 when NULL); u_prev = u0
+// f = f^eq(rho0, u0) as deviations (u0 = 0 and rho0 = 1 when NULL; both dense); u_prev = u0
 __global__ void k_lb_init(const LbArgs a, const float* __restrict__ u0, const float* __restrict__ rho0,
                           float* __restrict__ g, float* __restrict__ u_prev)
 {
-    const int n = blockIdx.x * blockDim.x + threadIdx.x;
-    if (n >= a.N) return;
-    const bool fl = lb_bit(a.fluid, n);
+    const int k = blockIdx.x * blockDim.x + threadIdx.x;
+    if (k >= a.NF) return;
+    const size_t NF = (size_t)a.NF;
+    const int n = __ldg(a.flist + k);
     float ux = 0.f, uy = 0.f, uz = 0.f, rho = 1.f;
-    if (u0 && fl) {
+    if (u0) {
         ux = u0[n];
         uy = u0[a.N + n];
         uz = u0[2 * a.N + n];
     }
-    if (rho0 && fl) rho = rho0[n];
+    if (rho0) rho = rho0[n];
     const float uu = ux * ux + uy * uy + uz * uz;
 #pragma unroll
     for (int i = 0; i < kQ; ++i) {
         const float cu = float(cx(i)) * ux + float(cy(i)) * uy + float(cz(i)) * uz;
         // f^eq - w = w [(rho - 1) + rho (3 cu + 4.5 cu^2 - 1.5 uu)]
-        g[(size_t)i * a.N + n] =
-            fl ? weight<float>(i) * ((rho - 1.0f) + rho * (3.0f * cu + 4.5f * cu * cu - 1.5f * uu)) : 0.0f;
+        g[(size_t)i * NF + k] = weight<float>(i) * ((rho - 1.0f) + rho * (3.0f * cu + 4.5f * cu * cu - 1.5f * uu));
     }
-    u_prev[n] = ux;
-    u_prev[a.N + n] = uy;
-    u_prev[2 * a.N + n] = uz;
+    u_prev[k] = ux;
+    u_prev[NF + k] = uy;
+    u_prev[2 * NF + k] = uz;
 }
 
 }  // namespace
@@ -169,7 +176,7 @@ extern "C" int lb_steady(const mp_geometry* geom, const double force[3], double 
     }
     cudaStream_t s = (cudaStream_t)stream_ptr;
     Geometry G;
-    int rc = build_geometry(geom, s, true, false, &G);
+    int rc = build_geometry(geom, s, true, true, &G);
     if (rc != MP_OK) return rc;
     // the body force acts on the largest connected fluid cluster: in a sealed pocket a
     // uniform force is balanced by pressure and the steady velocity is zero
@@ -180,12 +187,16 @@ extern "C" int lb_steady(const mp_geometry* geom, const double force[3], double 
         return rc;
     }
     const size_t N = (size_t)G.N;
+    const size_t NF = (size_t)(G.n_fluid > 0 ? G.n_fluid : 1);
     float *g0 = nullptr, *g1 = nullptr, *uprev = nullptr;
     unsigned long long* res_d = nullptr;
-    cudaError_t e = cudaMallocAsync((void**)&g0, sizeof(float) * kQ * N, s);
-    if (e == cudaSuccess) e = cudaMallocAsync((void**)&g1, sizeof(float) * kQ * N, s);
-    if (e == cudaSuccess) e = cudaMallocAsync((void**)&uprev, sizeof(float) * 3 * N, s);
+    cudaError_t e = cudaMallocAsync((void**)&g0, sizeof(float) * kQ * NF, s);
+    if (e == cudaSuccess) e = cudaMallocAsync((void**)&g1, sizeof(float) * kQ * NF, s);
+    if (e == cudaSuccess) e = cudaMallocAsync((void**)&uprev, sizeof(float) * 3 * NF, s);
     if (e == cudaSuccess) e = cudaMallocAsync((void**)&res_d, sizeof(unsigned long long), s);
+    // solid entries of the dense outputs stay zero; fluid entries are written at every check
+    if (e == cudaSuccess) e = cudaMemsetAsync(u_out, 0, sizeof(float) * 3 * N, s);
+    if (e == cudaSuccess && rho_out) e = cudaMemsetAsync(rho_out, 0, sizeof(float) * N, s);
     auto cleanup = [&]() {
         if (g0) cudaFreeAsync(g0, s);
         if (g1) cudaFreeAsync(g1, s);
@@ -204,14 +215,19 @@ extern "C" int lb_steady(const mp_geometry* geom, const double force[3], double 
     a.ny = G.ny;
     a.nz = G.nz;
     a.N = G.N;
+    a.NF = (int)G.n_fluid;
     a.fluid = G.fluid;
+    a.fbase = G.fbase;
+    a.flist = G.flist;
     a.forced = G.cluster;
     a.Fx = (float)force[0];
     a.Fy = (float)force[1];
     a.Fz = (float)force[2];
     a.inv_tau = (float)(1.0 / tau);
     a.guo = (float)(1.0 - 0.5 / tau);
-    const int blocks = (G.N + kLbThreads - 1) / kLbThreads;
+    // one thread per fluid node (at least one block, so that a medium without fluid still
+    // runs its checks: its residual is 0)
+    const int blocks = (int)((NF + kLbThreads - 1) / kLbThreads);
     k_lb_init<<<blocks, kLbThreads, 0, s>>>(a, u_init, rho_init, g0, uprev);
     e = cudaGetLastError();
     int64_t t = 0;
@@ -243,7 +259,7 @@ extern "C" int lb_steady(const mp_geometry* geom, const double force[3], double 
             // the mean of the last two iterates (g0 = t, g1 = t-1): same fixed point, and the
             // undamped period-2 modes that bounce-back sustains at confined nodes vanish
             if (t < max_steps) {
-                k_lb_mean<<<2 * 152 * 4, 256, 0, s>>>(g0, g1, (size_t)kQ * N);
+                k_lb_mean<<<2 * 152 * 4, 256, 0, s>>>(g0, g1, (size_t)kQ * NF);
                 e = cudaGetLastError();
             }
         }
