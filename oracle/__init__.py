@@ -204,14 +204,16 @@ def run(p: Problem, g: int = 0, nsteps: int = 0, init: str = "equilibrium") -> R
     return Run(Z, D, mf, ma, mi, P, Pa, Pg, Pga)
 
 
-def lb_init(solid: np.ndarray, u0: np.ndarray | None = None) -> np.ndarray:
-    """Populations f[19, nz, ny, nx] = f^eq(rho=1, u0) (oracle link order)."""
+def lb_init(solid: np.ndarray, u0: np.ndarray | None = None, rho0: np.ndarray | None = None) -> np.ndarray:
+    """Populations f[19, nz, ny, nx] = f^eq(rho0, u0) (rho0 = 1 and u0 = 0 by default;
+    oracle link order)."""
     s = np.ascontiguousarray(solid, dtype=np.uint8)
     nz, ny, nx = s.shape
     f = np.zeros((19,) + s.shape)
     u0c = None if u0 is None else np.ascontiguousarray(u0, dtype=np.float64)
+    r0c = None if rho0 is None else np.ascontiguousarray(rho0, dtype=np.float64)
     _load().or_lb_init(nx, ny, nz, _ptr(s, _u8p), _ptr(u0c, _dp) if u0c is not None else _dp(),
-                       _ptr(f, _dp))
+                       _ptr(r0c, _dp) if r0c is not None else _dp(), _ptr(f, _dp))
     return f
 
 
@@ -241,21 +243,27 @@ def lb_step(solid, f, force, tau=1.0, forced=None):
     return fo, u
 
 
-def lb_steady(solid, force, tau=1.0, tol=1e-7, max_steps=200000, check_every=100, u_init=None):
-    """Steady BGK flow, force on the largest fluid cluster; returns (u[3,nz,ny,nx], steps,
-    residual, converged)."""
+def lb_steady(solid, force, tau=1.0, tol=1e-7, max_steps=200000, check_every=100, u_init=None,
+              rho_init=None, with_rho=False):
+    """Steady BGK flow, force on the largest fluid cluster, started from f^eq(rho_init, u_init)
+    (rest and unit density by default); returns (u[3,nz,ny,nx], steps, residual, converged),
+    plus the final density rho[nz,ny,nx] (0 on solids) when with_rho."""
     s = np.ascontiguousarray(solid, dtype=np.uint8)
     nz, ny, nx = s.shape
     u = np.zeros((3,) + s.shape)
+    rho = np.zeros(s.shape)
     F = (ctypes.c_double * 3)(*[float(v) for v in force])
     steps = ctypes.c_int64()
     res = ctypes.c_double()
     ui = None if u_init is None else np.ascontiguousarray(u_init, dtype=np.float64)
+    ri = None if rho_init is None else np.ascontiguousarray(rho_init, dtype=np.float64)
     rc = _load().or_lb_steady(nx, ny, nz, _ptr(s, _u8p), F, ctypes.c_double(tau),
                               ctypes.c_double(tol), ctypes.c_int64(max_steps),
                               ctypes.c_int64(check_every),
-                              _ptr(ui, _dp) if ui is not None else _dp(), _ptr(u, _dp),
+                              _ptr(ui, _dp) if ui is not None else _dp(),
+                              _ptr(ri, _dp) if ri is not None else _dp(), _ptr(u, _dp), _ptr(rho, _dp),
                               ctypes.byref(steps), ctypes.byref(res))
     if rc < 0:
         raise ValueError("oracle LB rejected its input")
-    return u, steps.value, res.value, rc == 0
+    out = (u, steps.value, res.value, rc == 0)
+    return out + (rho,) if with_rho else out

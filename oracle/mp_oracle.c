@@ -544,7 +544,7 @@ static void lb_equilibrium(double rho, const double u[3], double* feq)
 }
 
 /* f = f^eq(rho = 1, u0) on fluid nodes (u0 = 0 when NULL), f = w_i on solid nodes */
-int or_lb_init(int nx, int ny, int nz, const uint8_t* solid, const double* u0, double* f)
+int or_lb_init(int nx, int ny, int nz, const uint8_t* solid, const double* u0, const double* rho0, double* f)
 {
     int64_t N = (int64_t)nx * ny * nz;
     for (int64_t n = 0; n < N; ++n) {
@@ -554,7 +554,7 @@ int or_lb_init(int nx, int ny, int nz, const uint8_t* solid, const double* u0, d
             u[1] = u0[N + n];
             u[2] = u0[2 * N + n];
         }
-        lb_equilibrium(1.0, u, feq);
+        lb_equilibrium((rho0 && !solid[n]) ? rho0[n] : 1.0, u, feq);
         for (int i = 0; i < NQ; ++i) f[(int64_t)i * N + n] = solid[n] ? WT[i] : feq[i];
     }
     return 0;
@@ -624,7 +624,8 @@ int or_lb_step(int nx, int ny, int nz, const uint8_t* solid, const uint8_t* forc
  * -1 on bad input; u_out gets u(steps). */
 int or_lb_steady(int nx, int ny, int nz, const uint8_t* solid, const double F[3], double tau,
                  double tol, int64_t max_steps, int64_t check_every, const double* u_init,
-                 double* u_out, int64_t* steps_out, double* residual_out)
+                 const double* rho_init, double* u_out, double* rho_out, int64_t* steps_out,
+                 double* residual_out)
 {
     int64_t N = (int64_t)nx * ny * nz;
     if (tau <= 0.5 || max_steps < 1 || check_every < 1) return -1;
@@ -638,7 +639,7 @@ int or_lb_steady(int nx, int ny, int nz, const uint8_t* solid, const double F[3]
         free(f); free(fn); free(u); free(uprev); free(forced);
         return -1;
     }
-    or_lb_init(nx, ny, nz, solid, u_init, f);
+    or_lb_init(nx, ny, nz, solid, u_init, rho_init, f);
     for (int64_t k = 0; k < 3 * N; ++k) uprev[k] = u_init ? u_init[k] : 0.0;
     for (int64_t n = 0; n < N; ++n)
         if (solid[n]) uprev[n] = uprev[N + n] = uprev[2 * N + n] = 0.0;
@@ -672,6 +673,13 @@ int or_lb_steady(int nx, int ny, int nz, const uint8_t* solid, const double F[3]
         memcpy(uprev, u, sizeof(double) * 3 * N);
     }
     memcpy(u_out, u, sizeof(double) * 3 * N);
+    if (rho_out) /* density of the final state: the collision conserves it, so sum f^post */
+        for (int64_t n = 0; n < N; ++n) {
+            double r = 0.0;
+            if (!solid[n])
+                for (int i = 0; i < NQ; ++i) r += f[(int64_t)i * N + n];
+            rho_out[n] = r;
+        }
     if (steps_out) *steps_out = t;
     if (residual_out) *residual_out = res;
     free(f); free(fn); free(u); free(uprev); free(forced);

@@ -130,3 +130,32 @@ def test_porous_medium_reaches_the_steady_criterion():
     for _ in range(200):
         f, u2 = oracle.lb_step(solid, f, F, 1.0, forced=inc)
     assert abs(u2[0][fl].mean() / u[0][fl].mean() - 1.0) < 1e-2
+
+
+def test_density_start_and_output_conserve_each_regions_mass():
+    """Eq. lb_evolution conserves the mass of every connected fluid region (streaming with
+    bounce-back moves it, the collision and the Guo term keep it). From rest the final density
+    of the forced channel sums to its node count and the sealed pockets keep density 1; a start
+    f^eq(rho*, u*) from the converged state stays at that flow (and needs no more steps than
+    from rest); a constant density offset in the start is the steady density's."""
+    solid = np.ones((9, 9, 12), dtype=np.uint8)
+    solid[2:6, 2:6, :] = 0
+    solid[7, 7, 3] = 0
+    solid[7, 1, 5:7] = 0
+    inc, _ = oracle.largest_cluster(solid)
+    ch = inc.astype(bool)
+    pockets = (solid == 0) & ~ch
+    F = (1e-5, 0.0, 0.0)
+    u, steps, res, conv, rho = oracle.lb_steady(solid, F, tol=1e-12, max_steps=20000, check_every=50, with_rho=True)
+    assert conv
+    assert abs(rho[ch].sum() - ch.sum()) < 1e-10
+    assert np.max(np.abs(rho[pockets] - 1.0)) < 1e-14
+    assert np.all(rho[solid.astype(bool)] == 0.0)
+    u2, s2, _, c2, rho2 = oracle.lb_steady(solid, F, tol=1e-12, max_steps=20000, check_every=50, u_init=u,
+                                            rho_init=rho, with_rho=True)
+    assert c2 and s2 <= steps
+    assert np.max(np.abs(u2 - u)) < 1e-9 * np.abs(u).max()
+    r0 = np.where(ch, 1.01, 1.0)
+    _, _, _, c3, rho3 = oracle.lb_steady(solid, F, tol=1e-12, max_steps=20000, check_every=50, rho_init=r0,
+                                         with_rho=True)
+    assert c3 and abs(rho3[ch].mean() - 1.01) < 1e-12
