@@ -6,6 +6,7 @@
 #include <stdint.h>
 
 #include <string>
+#include <utility>
 
 #include "../../include/mp.h"
 
@@ -71,6 +72,32 @@ struct Geometry {
     uint32_t* cluster = nullptr;  // bit set = node of the largest connected fluid cluster
     int64_t n_cluster = 0;
 };
+
+// Launch with programmatic dependent launch allowed: on the same stream the kernel may start
+// while the previous kernel drains (its blocks become resident and wait). Such a kernel calls
+// pdl_enter() first: it lets its own dependents start, then waits until the previous grid has
+// finished and its writes are visible, so nothing it reads or writes can race with it.
+template <typename... KArgs, typename... Args>
+cudaError_t launch_pdl(void (*kern)(KArgs...), dim3 grid, dim3 block, cudaStream_t s, Args&&... args)
+{
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = grid;
+    cfg.blockDim = block;
+    cfg.dynamicSmemBytes = 0;
+    cfg.stream = s;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    attr[0].val.programmaticStreamSerializationAllowed = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    return cudaLaunchKernelEx(&cfg, kern, std::forward<Args>(args)...);
+}
+
+__device__ __forceinline__ void pdl_enter()
+{
+    cudaTriggerProgrammaticLaunchCompletion();
+    cudaGridDependencySynchronize();
+}
 
 // Error reporting: the thread-local last-error text behind mp_last_error().
 void set_error(const std::string& msg);

@@ -56,6 +56,7 @@ __global__ void __launch_bounds__(kLbThreads)
               float* __restrict__ u_prev, float* __restrict__ u_out, float* __restrict__ rho_out,
               unsigned long long* __restrict__ res_bits)
 {
+    pdl_enter();  // launched with programmatic dependent launch: the previous step's populations
     const int k = blockIdx.x * kLbThreads + threadIdx.x;
     const size_t NF = (size_t)a.NF;
     double res = 0.0;
@@ -241,8 +242,9 @@ extern "C" int lb_steady(const mp_geometry* geom, const double force[3], double 
         else if ((t1 + 1) % check_every == 0 || t1 + 1 == max_steps)
             mode = 1;
         if (mode == 2) e = cudaMemsetAsync(res_d, 0, sizeof(unsigned long long), s);
-        k_lb_step<<<blocks, kLbThreads, 0, s>>>(a, g0, g1, mode, uprev, u_out, rho_out, res_d);
-        if (e == cudaSuccess) e = cudaGetLastError();
+        if (e == cudaSuccess)
+            e = launch_pdl(k_lb_step, dim3(blocks), dim3(kLbThreads), s, a, (const float*)g0, g1, mode, uprev, u_out,
+                           rho_out, res_d);
         float* tmp = g0;
         g0 = g1;
         g1 = tmp;

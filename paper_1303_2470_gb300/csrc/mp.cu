@@ -697,6 +697,9 @@ __global__ void __launch_bounds__(kThreads, min_blocks(kSingle, kThreads, sizeof
     k_step(const __grid_constant__ Args<T> a, const TS* __restrict__ P, TS* __restrict__ Pn,
            const TS* __restrict__ A, TS* __restrict__ An)
 {
+    // launched with programmatic dependent launch: wait for the previous step's fields, Z/D
+    // entries, partials and ticket before touching any of them
+    pdl_enter();
     // __grid_constant__: step_body reads the arguments through a reference, straight from
     // the constant bank (without it the whole structure would be copied per thread)
     step_body<T, TS, FP, kSingle, kThreads>(a, blockIdx.x, gridDim.x, P, Pn, A, An);
@@ -740,6 +743,7 @@ __global__ void __launch_bounds__(kB, kSingle ? 1536 / kB : min_blocks(false, kB
             b1 = g.bofs[j + 1];
         }
     }
+    pdl_enter();  // launched with programmatic dependent launch, like k_step
     const GroupPtrs p = g.ptrs[phase * g.n + c];
     step_body<float, float, FP, kSingle, kB>(g.args[c], (int)blockIdx.x - b0, b1 - b0, p.P, p.Pn, p.A, p.An);
 }
@@ -1122,8 +1126,8 @@ int step_typed(mp_ctx* c, long long n)
     auto launch = [&](long long count) {
         for (long long k = 0; k < count; ++k) {
             const int s = c->cur;
-            kern<<<c->blocks, kThreads, 0, c->stream>>>(a, (const TS*)c->P[s], (TS*)c->P[1 - s], (const TS*)c->A[s],
-                                                        (TS*)c->A[1 - s]);
+            launch_pdl(kern, dim3(c->blocks), dim3(kThreads), c->stream, a, (const TS*)c->P[s], (TS*)c->P[1 - s],
+                       (const TS*)c->A[s], (TS*)c->A[1 - s]);
             c->cur = 1 - s;
         }
     };
@@ -1501,11 +1505,11 @@ void launch_group_fp(mp_group* g)
 {
     const int blocks = g->ga.bofs[g->ctx.size()];
     if (g->block == 128)
-        k_step_group<FP, kSingle, 128><<<blocks, 128, 0, g->stream>>>(g->ga, g->phase);
+        launch_pdl(k_step_group<FP, kSingle, 128>, dim3(blocks), dim3(128), g->stream, g->ga, g->phase);
     else if (g->block == 512)
-        k_step_group<FP, kSingle, 512><<<blocks, 512, 0, g->stream>>>(g->ga, g->phase);
+        launch_pdl(k_step_group<FP, kSingle, 512>, dim3(blocks), dim3(512), g->stream, g->ga, g->phase);
     else
-        k_step_group<FP, kSingle, 256><<<blocks, 256, 0, g->stream>>>(g->ga, g->phase);
+        launch_pdl(k_step_group<FP, kSingle, 256>, dim3(blocks), dim3(256), g->stream, g->ga, g->phase);
 }
 
 // one grouped step: launch, then advance every context's phase, buffer and time
