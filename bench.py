@@ -346,12 +346,37 @@ def run_surrogate(args):
         out.append(rec)
         print(json.dumps(rec), flush=True)
         del u_cold, u_warm, u0, rho0, sd
+    # tensor throughput of the network's forward pass on a 128^3 box (all convolutions are
+    # 3x3x3: 2 * 27 * Cin * Cout FLOPs per voxel and layer)
+    n = 128
+    x0 = torch.zeros((1, n ** 3, 16), dtype=torch.bfloat16, device="cuda")
+    levels = {"e0a": 0, "e0b": 0, "e1a": 1, "e1b": 1, "b0": 2, "b1": 2, "d1a": 1, "d1b": 1, "d0a": 0, "d0b": 0,
+              "out": 0}
+    flops = sum(2.0 * 27 * cin * cout * (n >> levels[name]) ** 3 for name, cin, cout, _ in surrogate.LAYERS)
+    model.forward(x0, 1, (n, n, n))
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    for _ in range(5):
+        model.forward(x0, 1, (n, n, n))
+    e1.record()
+    torch.cuda.synchronize()
+    fwd_s = e0.elapsed_time(e1) / 5e3
+    peak = None
+    pp = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(pp):
+        peak = json.load(open(pp)).get("bf16_tflops")
+    tensor = {"kernel": "sg_conv3d forward pass, 128^3 box", "bound": "tensor", "achieved": flops / fwd_s / 1e12,
+              "peak": peak, "unit": "TFLOP/s", "frac": (flops / fwd_s / 1e12 / peak) if peak else None,
+              "flops": flops, "ms": fwd_s * 1e3,
+              "peak_source": "measured (MEASURED_PEAKS.json bf16_tflops, burst)" if peak else "unavailable"}
     line = {"metric": "LB steps to residual 1e-7: cold start / surrogate warm start", "unit": "ratio",
             "steps_factor": {c: float(np.mean([r["cold_steps"] / r["warm_steps"] for r in out if r["case"] == c]))
                              for c in dict.fromkeys(r["case"] for r in out)},
             "time_factor": {c: float(np.mean([r["cold_s"] / r["warm_s"] for r in out if r["case"] == c]))
                             for c in dict.fromkeys(r["case"] for r in out)},
             "cases": out,
+            "tensor_roofline": tensor,
             "model": {"n_params": meta["n_params"], "train_media": meta["n_train"], "size": meta["size"],
                       "iters": meta["iters"], "batch": meta["batch"], "train_seconds": meta["train_seconds"],
                       "final_loss": meta["loss_history"][-1][1]}}

@@ -14,12 +14,6 @@ namespace {
 
 typedef __nv_bfloat16 bf16;
 
-constexpr int kTM = 64;     // GEMM tile rows (voxels, or input channels for the weight gradient)
-constexpr int kTN = 64;     // GEMM tile columns (output channels)
-constexpr int kTK = 16;     // reduction step (channels, or voxels for the weight gradient)
-constexpr int kLd = 24;     // shared-memory row length in BF16 (48 bytes: conflict-free fragments)
-constexpr int kConvThreads = 128;
-
 __device__ __forceinline__ int wrap(int v, int n) { return v < 0 ? v + n : (v >= n ? v - n : v); }
 
 // D += A B for one m16n8k16 tile; fragments as the PTX ISA lays them out for .bf16:
@@ -36,22 +30,6 @@ __device__ __forceinline__ void mma16816(float (&d)[4], uint32_t a0, uint32_t a1
 
 __device__ __forceinline__ uint32_t lds32(const bf16* p) { return *reinterpret_cast<const uint32_t*>(p); }
 
-// one K step of a 64 x 64 tile: warp w owns rows 16w..16w+15, all 8 column tiles of 8
-__device__ __forceinline__ void tile_mma(const bf16 (*As)[kLd], const bf16 (*Bs)[kLd], float (&acc)[8][4], int ncols)
-{
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    const int g = lane >> 2, t = lane & 3, m = warp * 16;
-    const uint32_t a0 = lds32(&As[m + g][2 * t]), a1 = lds32(&As[m + g + 8][2 * t]);
-    const uint32_t a2 = lds32(&As[m + g][2 * t + 8]), a3 = lds32(&As[m + g + 8][2 * t + 8]);
-#pragma unroll
-    for (int nt = 0; nt < 8; ++nt) {
-        if (nt * 8 < ncols) {
-            const uint32_t b0 = lds32(&Bs[nt * 8 + g][2 * t]), b1 = lds32(&Bs[nt * 8 + g][2 * t + 8]);
-            mma16816(acc[nt], a0, a1, a2, a3, b0, b1);
-        }
-    }
-}
-
 struct ConvArgs {
     const bf16* x;
     const bf16* w;
@@ -61,17 +39,42 @@ struct ConvArgs {
     int D, H, W, V, K, N, sign, relu;
 };
 
-// Implicit GEMM: rows = voxels of one sample (blockIdx.z), columns = output channels, the
-// reduction runs over the 27 taps and the input channels in steps of 16. Each thread stages
-// one 16-byte piece of the A tile (a voxel's 8 channels at the shifted position) and one of
-// the B tile (8 input channels of one output channel of the tap).
-__global__ void __launch_bounds__(kConvThreads) k_conv(const ConvArgs a)
+// Forward (and transposed) convolution tile: 128 voxels x 64 output channels per block of
+// 8 warps (warp w: voxels 16w..16w+15, all eight column tiles), reduction over the 27 taps
+// and the input channels in stages of 32 (two m16n8k16 steps). The next stage's operands are
+// loaded into registers while the current one is multiplied, then stored to the other
+// shared buffer: one barrier per stage. Shared rows hold 40 BF16 (80 bytes), so the 8 rows
+// of a fragment load fall on distinct banks.
+constexpr int kCM = 128, kCN = 64, kCS = 32, kCLd = 40, kCThreads = 256;
+
+__device__ __forceinline__ void conv_stage_mma(const bf16 (*As)[kCLd], const bf16 (*Bs)[kCLd], float (&acc)[8][4],
+                                               int ncols)
 {
-    __shared__ __align__(16) bf16 As[kTM][kLd];
-    __shared__ __align__(16) bf16 Bs[kTN][kLd];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int g = lane >> 2, t = lane & 3, m = warp * 16;
+#pragma unroll
+    for (int kk = 0; kk < kCS; kk += 16) {
+        const uint32_t a0 = lds32(&As[m + g][kk + 2 * t]), a1 = lds32(&As[m + g + 8][kk + 2 * t]);
+        const uint32_t a2 = lds32(&As[m + g][kk + 2 * t + 8]), a3 = lds32(&As[m + g + 8][kk + 2 * t + 8]);
+#pragma unroll
+        for (int nt = 0; nt < 8; ++nt) {
+            if (nt * 8 < ncols) {
+                const uint32_t b0 = lds32(&Bs[nt * 8 + g][kk + 2 * t]), b1 = lds32(&Bs[nt * 8 + g][kk + 2 * t + 8]);
+                mma16816(acc[nt], a0, a1, a2, a3, b0, b1);
+            }
+        }
+    }
+}
+
+__global__ void __launch_bounds__(kCThreads) k_conv(const ConvArgs a)
+{
+    __shared__ __align__(16) bf16 As[2][kCM][kCLd];
+    __shared__ __align__(16) bf16 Bs[2][kCN][kCLd];
     const int tid = threadIdx.x;
-    const int v0 = blockIdx.x * kTM, n0 = blockIdx.y * kTN, b = blockIdx.z;
-    const int ar = tid >> 1, ah = (tid & 1) * 8;
+    const int v0 = blockIdx.x * kCM, n0 = blockIdx.y * kCN, b = blockIdx.z;
+    // this thread stages 16 channels of voxel row tid/2 (A) and 8 channels of column tid/4 (B)
+    const int ar = tid >> 1, ah = (tid & 1) * 16;
+    const int br = tid >> 2, bq = (tid & 3) * 8;
     const int va = v0 + ar;
     const bool vok = va < a.V;
     int xa = 0, ya = 0, za = 0;
@@ -80,30 +83,42 @@ __global__ void __launch_bounds__(kConvThreads) k_conv(const ConvArgs a)
         ya = (va / a.W) % a.H;
         za = va / (a.W * a.H);
     }
-    const bool nok = n0 + ar < a.N;
+    const bool nok = n0 + br < a.N;
     const bf16* xb = a.x + (size_t)b * a.V * a.K;
-    const int ncols = a.N - n0 < kTN ? a.N - n0 : kTN;
+    const int ncols = a.N - n0 < kCN ? a.N - n0 : kCN;
+    const int cstages = (a.K + kCS - 1) / kCS;  // channel stages per tap (K is a multiple of 16)
+    const int nst = 27 * cstages;
+    uint4 ra0, ra1, rb;
+    // global -> registers for stage st (zero outside the box of channels, voxels, columns)
+    auto fetch = [&](int st) {
+        const int tap = st / cstages, c0 = (st - tap * cstages) * kCS;
+        ra0 = ra1 = rb = make_uint4(0u, 0u, 0u, 0u);
+        if (vok && c0 + ah < a.K) {
+            const int dz = tap / 9 - 1, dy = (tap / 3) % 3 - 1, dx = tap % 3 - 1;
+            const int xs = wrap(xa + a.sign * dx, a.W), ys = wrap(ya + a.sign * dy, a.H), zs = wrap(za + a.sign * dz, a.D);
+            const bf16* p = xb + ((size_t)(zs * a.H + ys) * a.W + xs) * a.K + c0 + ah;
+            ra0 = *reinterpret_cast<const uint4*>(p);
+            ra1 = *reinterpret_cast<const uint4*>(p + 8);
+        }
+        if (nok && c0 + bq < a.K) rb = *reinterpret_cast<const uint4*>(a.w + ((size_t)tap * a.N + n0 + br) * a.K + c0 + bq);
+    };
+    auto stash = [&](int buf) {
+        *reinterpret_cast<uint4*>(&As[buf][ar][ah]) = ra0;
+        *reinterpret_cast<uint4*>(&As[buf][ar][ah + 8]) = ra1;
+        *reinterpret_cast<uint4*>(&Bs[buf][br][bq]) = rb;
+    };
     float acc[8][4];
 #pragma unroll
     for (int i = 0; i < 8; ++i) acc[i][0] = acc[i][1] = acc[i][2] = acc[i][3] = 0.0f;
-    for (int tap = 0; tap < 27; ++tap) {
-        const int dz = tap / 9 - 1, dy = (tap / 3) % 3 - 1, dx = tap % 3 - 1;
-        size_t src = 0;
-        if (vok) {
-            const int xs = wrap(xa + a.sign * dx, a.W), ys = wrap(ya + a.sign * dy, a.H), zs = wrap(za + a.sign * dz, a.D);
-            src = ((size_t)(zs * a.H + ys) * a.W + xs) * a.K;
-        }
-        const bf16* wt = a.w + ((size_t)tap * a.N + n0 + ar) * a.K;
-        for (int c0 = 0; c0 < a.K; c0 += kTK) {
-            uint4 av = make_uint4(0u, 0u, 0u, 0u), bv = make_uint4(0u, 0u, 0u, 0u);
-            if (vok) av = *reinterpret_cast<const uint4*>(xb + src + c0 + ah);
-            if (nok) bv = *reinterpret_cast<const uint4*>(wt + c0 + ah);
-            __syncthreads();
-            *reinterpret_cast<uint4*>(&As[ar][ah]) = av;
-            *reinterpret_cast<uint4*>(&Bs[ar][ah]) = bv;
-            __syncthreads();
-            tile_mma(As, Bs, acc, ncols);
-        }
+    fetch(0);
+    stash(0);
+    __syncthreads();
+    for (int st = 0; st < nst; ++st) {
+        const int cur = st & 1;
+        if (st + 1 < nst) fetch(st + 1);
+        conv_stage_mma(As[cur], Bs[cur], acc, ncols);
+        if (st + 1 < nst) stash(cur ^ 1);
+        __syncthreads();
     }
     const int lane = tid & 31, warp = tid >> 5, g = lane >> 2, t = lane & 3;
 #pragma unroll
@@ -136,53 +151,99 @@ struct WgradArgs {
     float* dw;
     int D, H, W, V, Cin, Cout;
     long long total;  // B * V voxels of the reduction
-    int chunk;        // voxels per block
+    int chunk;        // voxels per block (a multiple of 32)
+    int ci_tiles;     // tiles of 64 input channels
 };
 
-// Weight gradient of one tap (blockIdx.z % 27) over one chunk of voxels (blockIdx.z / 27):
-// rows = input channels, columns = output channels, reduction over voxels in steps of 16.
-// Thread (voxel kv = tid / 8, eight channels from 8 * (tid % 8)) stages one 16-byte piece of
-// x (at the shifted voxel) and of dy, transposed into the [channel][voxel] tiles.
-__global__ void __launch_bounds__(kConvThreads) k_wgrad(const WgradArgs a)
+// four 8x8 BF16 matrices from shared memory, transposed on the way (lanes 8j..8j+7 give the
+// row addresses of matrix j): each lane receives (M[2(l%4)][l/4], M[2(l%4)+1][l/4]) of every
+// matrix, which is the m16n8k16 fragment layout for an operand stored K-major
+__device__ __forceinline__ void ldsm_x4_t(uint32_t& r0, uint32_t& r1, uint32_t& r2, uint32_t& r3, const bf16* p)
 {
-    __shared__ __align__(16) bf16 As[kTM][kLd];
-    __shared__ __align__(16) bf16 Bs[kTN][kLd];
-    const int tid = threadIdx.x;
-    const int tap = blockIdx.z % 27;
-    const long long e0 = (long long)(blockIdx.z / 27) * a.chunk;
-    const int ci0 = blockIdx.x * kTM, co0 = blockIdx.y * kTN;
+    const uint32_t addr = (uint32_t)__cvta_generic_to_shared(p);
+    asm volatile("ldmatrix.sync.aligned.m8n8.x4.trans.shared.b16 {%0,%1,%2,%3}, [%4];"
+                 : "=r"(r0), "=r"(r1), "=r"(r2), "=r"(r3)
+                 : "r"(addr));
+}
+
+constexpr int kWM = 64, kWN = 64, kWS = 32, kWLd = 72, kWThreads = 128;
+
+// Weight gradient of one tap (blockIdx.x % 27) over one chunk of voxels (blockIdx.x / 27) for
+// one 64 x 64 tile of (input, output) channels (blockIdx.y): rows = input channels, columns =
+// output channels, reduction over voxels in stages of 32. Both operands stay channels-last in
+// shared memory ([voxel][channel], 144-byte rows) and the fragments come from transposing
+// loads. The next stage is fetched into registers during the current one's products.
+__global__ void __launch_bounds__(kWThreads) k_wgrad(const WgradArgs a)
+{
+    __shared__ __align__(16) bf16 Xs[2][kWS][kWLd];
+    __shared__ __align__(16) bf16 Gs[2][kWS][kWLd];
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const int tap = blockIdx.x % 27;
+    const long long e0 = (long long)(blockIdx.x / 27) * a.chunk;
+    const long long e1 = e0 + a.chunk < a.total ? e0 + a.chunk : a.total;
+    const int ci0 = (blockIdx.y % a.ci_tiles) * kWM, co0 = (blockIdx.y / a.ci_tiles) * kWN;
     const int dz = tap / 9 - 1, dy = (tap / 3) % 3 - 1, dx = tap % 3 - 1;
-    const int kv = tid >> 3, c8 = (tid & 7) * 8;
-    const int ncols = a.Cout - co0 < kTN ? a.Cout - co0 : kTN;
-    float acc[8][4];
-#pragma unroll
-    for (int i = 0; i < 8; ++i) acc[i][0] = acc[i][1] = acc[i][2] = acc[i][3] = 0.0f;
-    long long e1 = e0 + a.chunk;
-    if (e1 > a.total) e1 = a.total;
-    for (long long e = e0; e < e1; e += kTK) {
-        const long long ev = e + kv;
-        uint4 xv = make_uint4(0u, 0u, 0u, 0u), gv = make_uint4(0u, 0u, 0u, 0u);
+    const int lr = tid >> 2, lc = (tid & 3) * 16;  // this thread stages voxel row lr, 16 channels from lc
+    const int ncols = a.Cout - co0 < kWN ? a.Cout - co0 : kWN;
+    uint4 rx0, rx1, rg0, rg1;
+    auto fetch = [&](long long e) {
+        rx0 = rx1 = rg0 = rg1 = make_uint4(0u, 0u, 0u, 0u);
+        const long long ev = e + lr;
         if (ev < e1) {
             const long long bb = ev / a.V;
             const int v = (int)(ev - bb * a.V);
             const int xa = v % a.W, ya = (v / a.W) % a.H, za = v / (a.W * a.H);
             const int xs = wrap(xa + dx, a.W), ys = wrap(ya + dy, a.H), zs = wrap(za + dz, a.D);
             const size_t src = (size_t)bb * a.V + (size_t)((zs * a.H + ys) * a.W + xs);
-            if (ci0 + c8 < a.Cin) xv = *reinterpret_cast<const uint4*>(a.x + src * a.Cin + ci0 + c8);
-            if (co0 + c8 < a.Cout) gv = *reinterpret_cast<const uint4*>(a.dy + (size_t)ev * a.Cout + co0 + c8);
+            if (ci0 + lc < a.Cin) {
+                const bf16* p = a.x + src * a.Cin + ci0 + lc;
+                rx0 = *reinterpret_cast<const uint4*>(p);
+                rx1 = *reinterpret_cast<const uint4*>(p + 8);
+            }
+            if (co0 + lc < a.Cout) {
+                const bf16* p = a.dy + (size_t)ev * a.Cout + co0 + lc;
+                rg0 = *reinterpret_cast<const uint4*>(p);
+                rg1 = *reinterpret_cast<const uint4*>(p + 8);
+            }
         }
-        __syncthreads();
-        const bf16* xp = reinterpret_cast<const bf16*>(&xv);
-        const bf16* gp = reinterpret_cast<const bf16*>(&gv);
+    };
+    auto stash = [&](int buf) {
+        *reinterpret_cast<uint4*>(&Xs[buf][lr][lc]) = rx0;
+        *reinterpret_cast<uint4*>(&Xs[buf][lr][lc + 8]) = rx1;
+        *reinterpret_cast<uint4*>(&Gs[buf][lr][lc]) = rg0;
+        *reinterpret_cast<uint4*>(&Gs[buf][lr][lc + 8]) = rg1;
+    };
+    float acc[8][4];
 #pragma unroll
-        for (int j = 0; j < 8; ++j) {
-            As[c8 + j][kv] = xp[j];
-            Bs[c8 + j][kv] = gp[j];
+    for (int i = 0; i < 8; ++i) acc[i][0] = acc[i][1] = acc[i][2] = acc[i][3] = 0.0f;
+    const int nst = (int)((e1 - e0 + kWS - 1) / kWS);
+    const int r = lane & 7, mat = lane >> 3;
+    fetch(e0);
+    stash(0);
+    __syncthreads();
+    for (int st = 0; st < nst; ++st) {
+        const int cur = st & 1;
+        if (st + 1 < nst) fetch(e0 + (long long)(st + 1) * kWS);
+#pragma unroll
+        for (int kk = 0; kk < kWS; kk += 16) {
+            // A (rows = input channels of this warp): matrices (m0, k0) = (0,0), (8,0), (0,8), (8,8)
+            uint32_t a0, a1, a2, a3;
+            ldsm_x4_t(a0, a1, a2, a3, &Xs[cur][kk + (mat >> 1) * 8 + r][warp * 16 + (mat & 1) * 8]);
+#pragma unroll
+            for (int np = 0; np < 4; ++np) {
+                if (np * 16 < ncols) {
+                    // B for column tiles 2np and 2np+1: matrices (k0, n0) = (0,0), (8,0), (0,8), (8,8)
+                    uint32_t b0, b1, b2, b3;
+                    ldsm_x4_t(b0, b1, b2, b3, &Gs[cur][kk + (mat & 1) * 8 + r][np * 16 + (mat >> 1) * 8]);
+                    mma16816(acc[2 * np], a0, a1, a2, a3, b0, b1);
+                    if ((2 * np + 1) * 8 < ncols) mma16816(acc[2 * np + 1], a0, a1, a2, a3, b2, b3);
+                }
+            }
         }
+        if (st + 1 < nst) stash(cur ^ 1);
         __syncthreads();
-        tile_mma(As, Bs, acc, ncols);
     }
-    const int lane = tid & 31, warp = tid >> 5, g = lane >> 2, t = lane & 3;
+    const int g = lane >> 2, t = lane & 3;
 #pragma unroll
     for (int nt = 0; nt < 8; ++nt) {
         const int co = co0 + nt * 8 + 2 * t;
@@ -451,8 +512,8 @@ int sg_conv3d(const void* x, const void* w, const float* bias, void* y, float* y
         return MP_EINVAL;
     }
     ConvArgs a{(const bf16*)x, (const bf16*)w, bias, (bf16*)y, yf, D, H, W, D * H * W, K, N, sign, relu != 0};
-    dim3 grid((a.V + kTM - 1) / kTM, (N + kTN - 1) / kTN, B);
-    k_conv<<<grid, kConvThreads, 0, (cudaStream_t)stream>>>(a);
+    dim3 grid((a.V + kCM - 1) / kCM, (N + kCN - 1) / kCN, B);
+    k_conv<<<grid, kCThreads, 0, (cudaStream_t)stream>>>(a);
     MP_CUDA(cudaGetLastError());
     return MP_OK;
 }
@@ -465,14 +526,16 @@ int sg_conv3d_wgrad(const void* x, const void* dy, float* dw, float* dbias, int 
         set_error("sg_conv3d_wgrad: needs x, dy, dw, positive sizes, Cin and Cout multiples of 16");
         return MP_EINVAL;
     }
-    WgradArgs a{(const bf16*)x, (const bf16*)dy, dw, D, H, W, D * H * W, Cin, Cout, (long long)B * D * H * W, 2048};
+    const int ci_tiles = (Cin + kWM - 1) / kWM, co_tiles = (Cout + kWN - 1) / kWN;
+    WgradArgs a{(const bf16*)x, (const bf16*)dy, dw, D, H, W, D * H * W, Cin, Cout, (long long)B * D * H * W, 2048,
+                ci_tiles};
     const long long nchunk = (a.total + a.chunk - 1) / a.chunk;
-    if (nchunk * 27 > 2147483647LL) {
-        set_error("sg_conv3d_wgrad: too many voxels");
+    if (nchunk * 27 > 2147483647LL || ci_tiles * co_tiles > 65535) {
+        set_error("sg_conv3d_wgrad: too many voxels or channels");
         return MP_EINVAL;
     }
-    dim3 grid((Cin + kTM - 1) / kTM, (Cout + kTN - 1) / kTN, (unsigned)(nchunk * 27));
-    k_wgrad<<<grid, kConvThreads, 0, (cudaStream_t)stream>>>(a);
+    dim3 grid((unsigned)(nchunk * 27), (unsigned)(ci_tiles * co_tiles));
+    k_wgrad<<<grid, kWThreads, 0, (cudaStream_t)stream>>>(a);
     MP_CUDA(cudaGetLastError());
     if (dbias) {
         dim3 gb(grid1(a.total, 256), (Cout + 31) / 32);
