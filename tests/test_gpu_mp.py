@@ -226,3 +226,32 @@ def test_graph_replay_equals_plain_launches(mp):
         ctx.close()
     for a, b in zip(*out):
         assert np.array_equal(a[0], b[0]) and np.array_equal(a[1], b[1])
+
+
+@pytest.mark.parametrize("precision", ["fp32", "fp64", "fp16"])
+def test_maximum_species_count_all_directions(mp, precision):
+    """MP_MAX_SPECIES = 32 species with x, y and z moments in one context (the largest number
+    of chunk passes of the multi-species step) on a ragged 15x11x17 medium with flow, 120
+    steps: sampled species against the oracle (FP64 1e-11; FP32 and binary16 storage with
+    stochastic rounding 1e-4 and 2e-3 in D); 33 species are rejected."""
+    solid, _ = media.random_spheres((17, 11, 15), 2.5, 0.55, seed=21)
+    u = media.random_flow(solid, 0.02, seed=22).astype(np.float32)
+    Db, ka, kd = media.species(32, seed=23)
+    steps = 120
+    ctx = mp.mp_init_batch(solid, dev32(u), Db, ka, kd, precision=precision, directions="xyz", capacity=steps + 2,
+                           allow_negative=True)
+    mp.mp_step(ctx, steps)
+    for s in (0, 13, 31):
+        for g in range(3):
+            Z, D = mp.mp_vacf(ctx, s, g)
+            ref = oracle.run(oracle.Problem(solid, u.astype(np.float64), Db[s], ka[s], kd[s]), g=g, nsteps=steps)
+            if precision == "fp64":
+                assert _d_tol(D, ref.D) < 1e-11
+            else:
+                assert _z_tol(Z, ref.Z) < (1e-4 if precision == "fp32" else 2e-3)
+                assert _d_tol(D, ref.D) < (1e-4 if precision == "fp32" else 2e-3)
+    ctx.close()
+    Db33, ka33, kd33 = media.species(33, seed=24)
+    with pytest.raises(mp.MPError) as e:
+        mp.mp_init_batch(solid, dev32(u), Db33, ka33, kd33)
+    assert e.value.code == mp.MP_EINVAL
