@@ -1123,11 +1123,13 @@ int step_typed(mp_ctx* c, long long n)
     Args<T> a = make_args<T>(c);
     auto kern = c->FP == 2 ? (c->S == 1 ? k_step<T, TS, 2, true> : k_step<T, TS, 2, false>)
                            : (c->S == 1 ? k_step<T, TS, 4, true> : k_step<T, TS, 4, false>);
+    cudaError_t le = cudaSuccess;  // first failed launch, if any
     auto launch = [&](long long count) {
         for (long long k = 0; k < count; ++k) {
             const int s = c->cur;
-            launch_pdl(kern, dim3(c->blocks), dim3(kThreads), c->stream, a, (const TS*)c->P[s], (TS*)c->P[1 - s],
-                       (const TS*)c->A[s], (TS*)c->A[1 - s]);
+            const cudaError_t e = launch_pdl(kern, dim3(c->blocks), dim3(kThreads), c->stream, a, (const TS*)c->P[s],
+                                             (TS*)c->P[1 - s], (const TS*)c->A[s], (TS*)c->A[1 - s]);
+            if (e != cudaSuccess && le == cudaSuccess) le = e;
             c->cur = 1 - s;
         }
     };
@@ -1140,6 +1142,7 @@ int step_typed(mp_ctx* c, long long n)
                 e = cudaStreamEndCapture(c->stream, &c->graph[b]);
             }
             c->cur = b;
+            if (e == cudaSuccess && le != cudaSuccess) e = le;
             if (e == cudaSuccess) e = cudaGraphInstantiate(&c->exec[b], c->graph[b], 0);
             if (e != cudaSuccess) return cuda_fail(e, "mp_step: graph capture");
         }
@@ -1150,6 +1153,7 @@ int step_typed(mp_ctx* c, long long n)
     }
     launch(n);
     c->t += n;
+    if (le != cudaSuccess) return cuda_fail(le, "mp_step: launch");
     MP_CUDA(cudaGetLastError());
     return MP_OK;
 }
@@ -1501,30 +1505,28 @@ void group_set_block(mp_group* g, int block)
 }
 
 template <int FP, bool kSingle>
-void launch_group_fp(mp_group* g)
+cudaError_t launch_group_fp(mp_group* g)
 {
     const int blocks = g->ga.bofs[g->ctx.size()];
     if (g->block == 128)
-        launch_pdl(k_step_group<FP, kSingle, 128>, dim3(blocks), dim3(128), g->stream, g->ga, g->phase);
-    else if (g->block == 512)
-        launch_pdl(k_step_group<FP, kSingle, 512>, dim3(blocks), dim3(512), g->stream, g->ga, g->phase);
-    else
-        launch_pdl(k_step_group<FP, kSingle, 256>, dim3(blocks), dim3(256), g->stream, g->ga, g->phase);
+        return launch_pdl(k_step_group<FP, kSingle, 128>, dim3(blocks), dim3(128), g->stream, g->ga, g->phase);
+    if (g->block == 512)
+        return launch_pdl(k_step_group<FP, kSingle, 512>, dim3(blocks), dim3(512), g->stream, g->ga, g->phase);
+    return launch_pdl(k_step_group<FP, kSingle, 256>, dim3(blocks), dim3(256), g->stream, g->ga, g->phase);
 }
 
 // one grouped step: launch, then advance every context's phase, buffer and time
-void group_launch(mp_group* g, bool advance_ctx)
+cudaError_t group_launch(mp_group* g, bool advance_ctx)
 {
-    if (g->FP == 2)
-        g->single ? launch_group_fp<2, true>(g) : launch_group_fp<2, false>(g);
-    else
-        g->single ? launch_group_fp<4, true>(g) : launch_group_fp<4, false>(g);
+    const cudaError_t e = g->FP == 2 ? (g->single ? launch_group_fp<2, true>(g) : launch_group_fp<2, false>(g))
+                                     : (g->single ? launch_group_fp<4, true>(g) : launch_group_fp<4, false>(g));
     g->phase ^= 1;
     if (advance_ctx)
         for (mp_ctx* c : g->ctx) {
             c->cur ^= 1;
             c->t += 1;
         }
+    return e;
 }
 
 int group_sync_in(mp_group* g)
@@ -1584,9 +1586,9 @@ int group_autotune(mp_group* g, int steps)
             if (e == cudaSuccess) e = cudaMemcpyAsync(bA[c], x->A[x->cur], nA[c], cudaMemcpyDeviceToDevice, g->stream);
         }
         group_set_block(g, cand[k]);
-        group_launch(g, false);  // warm-up launch of this configuration
+        if (e == cudaSuccess) e = group_launch(g, false);  // warm-up launch of this configuration
         if (e == cudaSuccess) e = cudaEventRecord(e0, g->stream);
-        for (int s2 = 0; s2 < steps; ++s2) group_launch(g, false);
+        for (int s2 = 0; s2 < steps && e == cudaSuccess; ++s2) e = group_launch(g, false);
         if (e == cudaSuccess) e = cudaEventRecord(e1, g->stream);
         if (e == cudaSuccess) e = cudaEventSynchronize(e1);
         float ms = 0.f;
@@ -1717,8 +1719,13 @@ int mp_group_create(mp_group** out, mp_ctx* const* ctxs, int n, int graph_steps,
         g->phase = 0;
         e = cudaStreamBeginCapture(g->stream, cudaStreamCaptureModeThreadLocal);
         if (e == cudaSuccess) {
-            for (int k = 0; k < graph_steps; ++k) group_launch(g, false);
+            cudaError_t le = cudaSuccess;
+            for (int k = 0; k < graph_steps; ++k) {
+                const cudaError_t e2 = group_launch(g, false);
+                if (le == cudaSuccess) le = e2;
+            }
             e = cudaStreamEndCapture(g->stream, &g->graph);
+            if (e == cudaSuccess) e = le;
         }
         if (e == cudaSuccess) e = cudaGraphInstantiate(&g->exec, g->graph, 0);
         g->phase = phase0;
@@ -1747,7 +1754,7 @@ int mp_group_step(mp_group* g, int64_t n)
         }
     if (int rc = group_sync_in(g)) return rc;
     while (n > 0 && g->graph_steps > 0 && g->phase != 0) {
-        group_launch(g, true);
+        MP_CUDA(group_launch(g, true));
         --n;
     }
     while (g->graph_steps > 0 && n >= g->graph_steps) {
@@ -1759,7 +1766,7 @@ int mp_group_step(mp_group* g, int64_t n)
         n -= g->graph_steps;
     }
     while (n > 0) {
-        group_launch(g, true);
+        MP_CUDA(group_launch(g, true));
         --n;
     }
     MP_CUDA(cudaGetLastError());
