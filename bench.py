@@ -65,7 +65,7 @@ UNIT = "node-species updates/s"
 TRAFFIC = {
     # ncu --set full, python bench.py --profile, k_step<float,2,1> launch 11 (caches flushed
     # by ncu before the capture, so this is the cold-L2 traffic of one launch)
-    "k_step<float>": {"bytes_per_launch": 48_621_312 + 1_398_272, "src_sha": "39b0f916ab378d67"},
+    "k_step<float>": {"bytes_per_launch": 48_607_488 + 1_392_640, "src_sha": "cd4af1701d41b82f"},
 }
 
 
