@@ -350,8 +350,8 @@ def run_surrogate(args):
     # 3x3x3: 2 * 27 * Cin * Cout FLOPs per voxel and layer)
     n = 128
     x0 = torch.zeros((1, n ** 3, 16), dtype=torch.bfloat16, device="cuda")
-    levels = {"e0a": 0, "e0b": 0, "e1a": 1, "e1b": 1, "b0": 2, "b1": 2, "d1a": 1, "d1b": 1, "d0a": 0, "d0b": 0,
-              "out": 0}
+    levels = {"e0a": 0, "e0b": 0, "e1a": 1, "e1b": 1, "e2a": 2, "e2b": 2, "b0": 3, "b1": 3, "d2a": 2, "d2b": 2,
+              "d1a": 1, "d1b": 1, "d0a": 0, "d0b": 0, "out": 0}
     flops = sum(2.0 * 27 * cin * cout * (n >> levels[name]) ** 3 for name, cin, cout, _ in surrogate.LAYERS)
     model.forward(x0, 1, (n, n, n))
     torch.cuda.synchronize()

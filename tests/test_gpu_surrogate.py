@@ -163,8 +163,10 @@ def _torch_net(params, x):
     h = x.permute(0, 4, 1, 2, 3)
     s0 = conv("e0b", conv("e0a", h))
     s1 = conv("e1b", conv("e1a", F.avg_pool3d(s0, 2)))
-    c2 = conv("b1", conv("b0", F.avg_pool3d(s1, 2)))
-    e1 = conv("d1b", conv("d1a", F.interpolate(c2, scale_factor=2)) + s1)
+    s2 = conv("e2b", conv("e2a", F.avg_pool3d(s1, 2)))
+    c3 = conv("b1", conv("b0", F.avg_pool3d(s2, 2)))
+    e2 = conv("d2b", conv("d2a", F.interpolate(c3, scale_factor=2)) + s2)
+    e1 = conv("d1b", conv("d1a", F.interpolate(e2, scale_factor=2)) + s1)
     e0 = conv("d0b", conv("d0a", F.interpolate(e1, scale_factor=2)) + s0)
     return conv("out", e0, relu=False).permute(0, 2, 3, 4, 1)
 
@@ -172,7 +174,7 @@ def _torch_net(params, x):
 def test_network_loss_and_gradients_match_autograd(mp):
     """Forward, masked loss and every parameter gradient of the whole network on an 8^3 box
     against PyTorch autograd of the same network with the same weights (BF16 activations and
-    gradients through eleven layers: outputs within 2 %, all gradients within 5 % in norm)."""
+    gradients through fifteen layers: outputs within 2 %, all gradients within 6 % in norm)."""
     from paper_1303_2470_gb300 import surrogate
     model = surrogate.Surrogate(seed=5)
     for t in model.p.values():                                  # keep the FP32 masters exactly BF16
@@ -205,8 +207,8 @@ def test_network_loss_and_gradients_match_autograd(mp):
     assert abs(loss.item() / lr_.item() - 1.0) < 2e-2
     # Each kernel is checked alone above (1e-5); this test checks the wiring (layer order,
     # skips, pooling, ReLU masks), whose mistakes give errors of order one. Over all
-    # parameters the relative error is bounded by the BF16 stages: the deepest gradient passes
-    # 11 forward and 11 backward roundings of 2^-9, 22 x 2^-9 = 4.3 %, so 5 %. Per tensor the
+    # parameters the relative error is bounded by the BF16 stages: a gradient passes at most
+    # 15 forward and 15 backward roundings of 2^-9, 30 x 2^-9 = 5.9 %, so 6 %. Per tensor the
     # bound is looser (15 %): a bias gradient is a sum over voxels whose terms cancel, so its
     # rounding error scales with the sum of their magnitudes, not with the sum itself.
     num, den = 0.0, 0.0
@@ -219,7 +221,7 @@ def test_network_loss_and_gradients_match_autograd(mp):
             assert e < 0.15 * r, (name, key, e / r)
             num += e * e
             den += r * r
-    assert np.sqrt(num / den) < 5e-2
+    assert np.sqrt(num / den) < 6e-2
 
 
 WEIGHTS = os.path.join(os.path.dirname(os.path.dirname(os.path.abspath(__file__))), "paper_1303_2470_gb300",

@@ -23,7 +23,7 @@ def test_weights_match_the_network():
         assert W.shape == (27, cin, cout) and W.dtype == np.float32 and np.all(np.isfinite(W))
         assert b.shape == (cout,) and np.all(np.isfinite(b))
         n += W.size + b.size
-    assert n == meta["n_params"] == 1_300_112
+    assert n == meta["n_params"] == 2_351_120
     assert meta["s_u"] > 0 and meta["s_rho"] > 0 and meta["force"] == 1e-5
     hist = [v for _, v in meta["val_history"]]
     assert len(hist) >= 2 and hist[-1] < hist[0]          # the held-out loss fell while training
