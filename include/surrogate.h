@@ -2,8 +2,8 @@
  * surrogate.h -- C ABI of the kernels behind the learned warm start of lb_steady: a small
  * 3D convolutional encoder-decoder that maps a porous medium to an estimate of its steady
  * flow and density, used only as the starting state (u_init, rho_init) of lb_steady (the
- * plain LB runs to the same residual from there, so it remains the judge of convergence). The paper has no
- * counterpart; it solves the LB from rest (Sec. "Introduction", Eq. lb_evolution).
+ * plain LB runs to the same residual from there, so it alone decides convergence). The paper
+ * has no counterpart; it solves the LB from rest (Sec. "Introduction", Eq. lb_evolution).
  *
  * Conventions (in addition to those of mp.h, whose status codes and mp_last_error() these
  * functions share; they are exported by the same library, libmp):

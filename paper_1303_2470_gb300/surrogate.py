@@ -1,9 +1,9 @@
 """Learned warm start for lb_steady: a small 3D convolutional encoder-decoder that maps a
 porous medium (its fluid and forced-cluster masks) to an estimate of the steady LB state
 (velocity and density) driven by a unit body force, used only as the starting state of
-lb_steady. The plain LB still runs to the same residual, so it remains the judge; a poor
-estimate costs steps, never accuracy. The paper solves the LB from rest; this is a GB300-side
-acceleration of that solve.
+lb_steady. The plain LB still runs to the same residual, so it alone decides convergence; a
+poor estimate costs steps, never accuracy. The paper solves the LB from rest; this is a
+GB300-side acceleration of that solve.
 
 The density matters as much as the velocity: restarted from f^eq(rho = 1, u*) with the
 exact steady velocity u*, the LB of a 128^3 porous medium needs as many steps as from rest

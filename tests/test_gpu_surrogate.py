@@ -1,6 +1,6 @@
 """Kernels of the learned LB warm start (include/surrogate.h) against plain PyTorch FP32
 references of the same operations (CPU), and the warm start itself against the cold-start
-LB, which stays the judge.
+LB, which alone decides convergence.
 
 Tolerances follow from the arithmetic: operands are BF16 (the references get the same
 BF16-rounded values), products accumulate in FP32, and BF16 outputs carry a relative
