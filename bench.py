@@ -407,6 +407,24 @@ def run_profile_batched():
     return 0
 
 
+def run_profile_surrogate():
+    """Two forward passes of the trained warm-start network on a 128^3 box (15 `k_conv`
+    launches each, in layer order e0a .. out), no timing: for ncu captures of the tensor-core
+    convolution (the second pass's d0a, 64 -> 32 channels at full resolution, is launch 27)."""
+    import torch
+    from paper_1303_2470_gb300 import build
+    build.build()
+    from paper_1303_2470_gb300 import surrogate
+    model, _ = surrogate.load()
+    n = 128
+    x0 = torch.zeros((1, n ** 3, 16), dtype=torch.bfloat16, device="cuda")
+    for _ in range(2):
+        model.forward(x0, 1, (n, n, n))
+    torch.cuda.synchronize()
+    print(json.dumps({"profile_surrogate": "ok", "layers": [name for name, _, _, _ in surrogate.LAYERS]}))
+    return 0
+
+
 def run_profile_case():
     """The workload's kernels on the same 128^3 medium, briefly, for ncu --set full
     captures (python bench.py --profile): LB launches 1-30, k_init, MP launches 1-20."""
@@ -443,6 +461,8 @@ def main():
                          "steps to steady from the learned warm start vs the cold start")
     ap.add_argument("--profile-batched", action="store_true",
                     help="short grouped run (96^3 and 128^3 media x 16 species) for ncu captures")
+    ap.add_argument("--profile-surrogate", action="store_true",
+                    help="two forward passes of the warm-start network on a 128^3 box for ncu captures")
     ap.add_argument("--profile", action="store_true",
                     help="short run of the same medium and kernels for ncu captures: 30 LB steps, "
                          "mp_init and 20 MP steps, no timing")
@@ -454,6 +474,8 @@ def main():
         return run_profile_case()
     if args.profile_batched:
         return run_profile_batched()
+    if args.profile_surrogate:
+        return run_profile_surrogate()
     if args.workload == "batched":
         return run_batched(args)
     if args.workload == "surrogate":
