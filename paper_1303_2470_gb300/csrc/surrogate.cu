@@ -28,8 +28,6 @@ __device__ __forceinline__ void mma16816(float (&d)[4], uint32_t a0, uint32_t a1
         : "r"(a0), "r"(a1), "r"(a2), "r"(a3), "r"(b0), "r"(b1));
 }
 
-__device__ __forceinline__ uint32_t lds32(const bf16* p) { return *reinterpret_cast<const uint32_t*>(p); }
-
 struct ConvArgs {
     const bf16* x;
     const bf16* w;
@@ -39,107 +37,160 @@ struct ConvArgs {
     int D, H, W, V, K, N, sign, relu;
 };
 
-// Forward (and transposed) convolution tile: 128 voxels x 64 output channels per block of
-// 8 warps (warp w: voxels 16w..16w+15, all eight column tiles), reduction over the 27 taps
-// and the input channels in stages of 32 (two m16n8k16 steps). The next stage's operands are
-// loaded into registers while the current one is multiplied, then stored to the other
-// shared buffer: one barrier per stage. Shared rows hold 40 BF16 (80 bytes), so the 8 rows
-// of a fragment load fall on distinct banks.
-constexpr int kCM = 128, kCN = 64, kCS = 32, kCLd = 40, kCThreads = 256;
+// four 8x8 BF16 matrices from shared memory (lanes 8j..8j+7 give the row addresses of
+// matrix j): each lane receives (M[l/4][2(l%4)], M[l/4][2(l%4)+1]) of every matrix, which is
+// the m16n8k16 fragment layout of A (row-major) and of B stored as [n][k]
+__device__ __forceinline__ void ldsm_x4(uint32_t& r0, uint32_t& r1, uint32_t& r2, uint32_t& r3, const bf16* p)
+{
+    const uint32_t addr = (uint32_t)__cvta_generic_to_shared(p);
+    asm volatile("ldmatrix.sync.aligned.m8n8.x4.shared.b16 {%0,%1,%2,%3}, [%4];"
+                 : "=r"(r0), "=r"(r1), "=r"(r2), "=r"(r3)
+                 : "r"(addr)
+                 : "memory");
+}
 
-__device__ __forceinline__ void conv_stage_mma(const bf16 (*As)[kCLd], const bf16 (*Bs)[kCLd], float (&acc)[8][4],
-                                               int ncols)
+// Forward (and transposed) convolution tile: BM = 128 MT voxels x BN = 8 NT output channels
+// per block of 8 warps (warp w: voxels 16 MT w .. 16 MT (w + 1) - 1, all NT column tiles),
+// reduction over the 27 taps and the input channels in stages of 32 (two m16n8k16 steps).
+// Two shapes: 128 x 64 (MT = 1, NT = 8) for N > 32 and 256 x 32 (MT = 2, NT = 4) for
+// N <= 32, so that the full-resolution 32-channel layers fill their tiles and each B
+// fragment feeds two products. The next stage's operands are loaded into registers while the
+// current one is multiplied, then stored to the other shared buffer: one barrier per stage.
+// Shared rows hold 40 BF16 (80 bytes), so the eight 16-byte rows of an ldmatrix phase, and
+// the staging stores of eight consecutive rows, fall on distinct banks.
+constexpr int kCS = 32, kCLd = 40, kCThreads = 256;
+
+template <int MT, int NT>
+__device__ __forceinline__ void conv_stage_mma(const bf16 (*As)[kCLd], const bf16 (*Bs)[kCLd],
+                                               float (&acc)[MT][NT][4], int ncols)
 {
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    const int g = lane >> 2, t = lane & 3, m = warp * 16;
+    const int m0 = warp * 16 * MT;
+    // A: matrices (rows 0-7, k 0-7), (rows 8-15, k 0-7), (rows 0-7, k 8-15), (rows 8-15, k 8-15)
+    const int ar = (lane & 7) + ((lane >> 3) & 1) * 8, ac = (lane >> 4) * 8;
+    // B ([n][k]): matrices (tile nt, k 0-7), (nt, k 8-15), (nt + 1, k 0-7), (nt + 1, k 8-15)
+    const int br = (lane & 7) + (lane >> 4) * 8, bc = ((lane >> 3) & 1) * 8;
 #pragma unroll
     for (int kk = 0; kk < kCS; kk += 16) {
-        const uint32_t a0 = lds32(&As[m + g][kk + 2 * t]), a1 = lds32(&As[m + g + 8][kk + 2 * t]);
-        const uint32_t a2 = lds32(&As[m + g][kk + 2 * t + 8]), a3 = lds32(&As[m + g + 8][kk + 2 * t + 8]);
+        uint32_t af[MT][4];
 #pragma unroll
-        for (int nt = 0; nt < 8; ++nt) {
-            if (nt * 8 < ncols) {
-                const uint32_t b0 = lds32(&Bs[nt * 8 + g][kk + 2 * t]), b1 = lds32(&Bs[nt * 8 + g][kk + 2 * t + 8]);
-                mma16816(acc[nt], a0, a1, a2, a3, b0, b1);
+        for (int mt = 0; mt < MT; ++mt)
+            ldsm_x4(af[mt][0], af[mt][1], af[mt][2], af[mt][3], &As[m0 + mt * 16 + ar][kk + ac]);
+#pragma unroll
+        for (int nt = 0; nt < NT; nt += 2) {
+            if (nt * 8 < ncols) {  // ncols is a multiple of 16: both tiles of the pair or neither
+                uint32_t b0, b1, b2, b3;
+                ldsm_x4(b0, b1, b2, b3, &Bs[nt * 8 + br][kk + bc]);
+#pragma unroll
+                for (int mt = 0; mt < MT; ++mt) {
+                    mma16816(acc[mt][nt], af[mt][0], af[mt][1], af[mt][2], af[mt][3], b0, b1);
+                    mma16816(acc[mt][nt + 1], af[mt][0], af[mt][1], af[mt][2], af[mt][3], b2, b3);
+                }
             }
         }
     }
 }
 
+template <int MT, int NT>
 __global__ void __launch_bounds__(kCThreads) k_conv(const ConvArgs a)
 {
-    __shared__ __align__(16) bf16 As[2][kCM][kCLd];
-    __shared__ __align__(16) bf16 Bs[2][kCN][kCLd];
+    constexpr int BM = 128 * MT, BN = 8 * NT;
+    constexpr int AP = 2 * BM / kCThreads;  // A pieces (16 channels of one voxel) per thread
+    static_assert(AP * kCThreads == 2 * BM && BN * 4 <= kCThreads, "staging shape");
+    __shared__ __align__(16) bf16 As[2][BM][kCLd];
+    __shared__ __align__(16) bf16 Bs[2][BN][kCLd];
     const int tid = threadIdx.x;
-    const int v0 = blockIdx.x * kCM, n0 = blockIdx.y * kCN, b = blockIdx.z;
-    // this thread stages 16 channels of voxel row tid/2 (A) and 8 channels of column tid/4 (B)
-    const int ar = tid >> 1, ah = (tid & 1) * 16;
-    const int br = tid >> 2, bq = (tid & 3) * 8;
-    const int va = v0 + ar;
-    const bool vok = va < a.V;
-    int xa = 0, ya = 0, za = 0;
-    if (vok) {
-        xa = va % a.W;
-        ya = (va / a.W) % a.H;
-        za = va / (a.W * a.H);
+    const int v0 = blockIdx.x * BM, n0 = blockIdx.y * BN, b = blockIdx.z;
+    // A piece p = tid + 256 i: voxel row p % BM, channels 16 (p / BM) .. +15 of the stage;
+    // B: column row tid % BN, channels 8 (tid / BN) .. +7 (threads below 4 BN)
+    int ar[AP], ah[AP], xa[AP], ya[AP], za[AP];
+    bool vok[AP];
+#pragma unroll
+    for (int i = 0; i < AP; ++i) {
+        const int p = tid + kCThreads * i;
+        ar[i] = p % BM;
+        ah[i] = (p / BM) * 16;
+        const int va = v0 + ar[i];
+        vok[i] = va < a.V;
+        xa[i] = ya[i] = za[i] = 0;
+        if (vok[i]) {
+            xa[i] = va % a.W;
+            ya[i] = (va / a.W) % a.H;
+            za[i] = va / (a.W * a.H);
+        }
     }
-    const bool nok = n0 + br < a.N;
+    const bool bthr = tid < BN * 4;
+    const int br = tid % BN, bq = (tid / BN) * 8;
+    const bool nok = bthr && n0 + br < a.N;
     const bf16* xb = a.x + (size_t)b * a.V * a.K;
-    const int ncols = a.N - n0 < kCN ? a.N - n0 : kCN;
+    const int ncols = a.N - n0 < BN ? a.N - n0 : BN;
     const int cstages = (a.K + kCS - 1) / kCS;  // channel stages per tap (K is a multiple of 16)
     const int nst = 27 * cstages;
-    uint4 ra0, ra1, rb;
+    uint4 ra[AP][2], rb;
     // global -> registers for stage st (zero outside the box of channels, voxels, columns)
     auto fetch = [&](int st) {
         const int tap = st / cstages, c0 = (st - tap * cstages) * kCS;
-        ra0 = ra1 = rb = make_uint4(0u, 0u, 0u, 0u);
-        if (vok && c0 + ah < a.K) {
-            const int dz = tap / 9 - 1, dy = (tap / 3) % 3 - 1, dx = tap % 3 - 1;
-            const int xs = wrap(xa + a.sign * dx, a.W), ys = wrap(ya + a.sign * dy, a.H), zs = wrap(za + a.sign * dz, a.D);
-            const bf16* p = xb + ((size_t)(zs * a.H + ys) * a.W + xs) * a.K + c0 + ah;
-            ra0 = *reinterpret_cast<const uint4*>(p);
-            ra1 = *reinterpret_cast<const uint4*>(p + 8);
+        const int dz = tap / 9 - 1, dy = (tap / 3) % 3 - 1, dx = tap % 3 - 1;
+#pragma unroll
+        for (int i = 0; i < AP; ++i) {
+            ra[i][0] = ra[i][1] = make_uint4(0u, 0u, 0u, 0u);
+            if (vok[i] && c0 + ah[i] < a.K) {
+                const int xs = wrap(xa[i] + a.sign * dx, a.W), ys = wrap(ya[i] + a.sign * dy, a.H);
+                const int zs = wrap(za[i] + a.sign * dz, a.D);
+                const bf16* p = xb + ((size_t)(zs * a.H + ys) * a.W + xs) * a.K + c0 + ah[i];
+                ra[i][0] = *reinterpret_cast<const uint4*>(p);
+                ra[i][1] = *reinterpret_cast<const uint4*>(p + 8);
+            }
         }
+        rb = make_uint4(0u, 0u, 0u, 0u);
         if (nok && c0 + bq < a.K) rb = *reinterpret_cast<const uint4*>(a.w + ((size_t)tap * a.N + n0 + br) * a.K + c0 + bq);
     };
     auto stash = [&](int buf) {
-        *reinterpret_cast<uint4*>(&As[buf][ar][ah]) = ra0;
-        *reinterpret_cast<uint4*>(&As[buf][ar][ah + 8]) = ra1;
-        *reinterpret_cast<uint4*>(&Bs[buf][br][bq]) = rb;
-    };
-    float acc[8][4];
 #pragma unroll
-    for (int i = 0; i < 8; ++i) acc[i][0] = acc[i][1] = acc[i][2] = acc[i][3] = 0.0f;
+        for (int i = 0; i < AP; ++i) {
+            *reinterpret_cast<uint4*>(&As[buf][ar[i]][ah[i]]) = ra[i][0];
+            *reinterpret_cast<uint4*>(&As[buf][ar[i]][ah[i] + 8]) = ra[i][1];
+        }
+        if (bthr) *reinterpret_cast<uint4*>(&Bs[buf][br][bq]) = rb;
+    };
+    float acc[MT][NT][4];
+#pragma unroll
+    for (int mt = 0; mt < MT; ++mt)
+#pragma unroll
+        for (int i = 0; i < NT; ++i) acc[mt][i][0] = acc[mt][i][1] = acc[mt][i][2] = acc[mt][i][3] = 0.0f;
     fetch(0);
     stash(0);
     __syncthreads();
     for (int st = 0; st < nst; ++st) {
         const int cur = st & 1;
         if (st + 1 < nst) fetch(st + 1);
-        conv_stage_mma(As[cur], Bs[cur], acc, ncols);
+        conv_stage_mma<MT, NT>(As[cur], Bs[cur], acc, ncols);
         if (st + 1 < nst) stash(cur ^ 1);
         __syncthreads();
     }
     const int lane = tid & 31, warp = tid >> 5, g = lane >> 2, t = lane & 3;
 #pragma unroll
-    for (int nt = 0; nt < 8; ++nt) {
+    for (int nt = 0; nt < NT; ++nt) {
         const int col = n0 + nt * 8 + 2 * t;
         if (col >= a.N) continue;
         const float b0 = a.bias ? a.bias[col] : 0.0f, b1 = a.bias ? a.bias[col + 1] : 0.0f;
 #pragma unroll
-        for (int h = 0; h < 2; ++h) {
-            const int v = v0 + warp * 16 + g + 8 * h;
-            if (v >= a.V) continue;
-            float r0 = acc[nt][2 * h] + b0, r1 = acc[nt][2 * h + 1] + b1;
-            if (a.relu) {
-                r0 = fmaxf(r0, 0.0f);
-                r1 = fmaxf(r1, 0.0f);
-            }
-            const size_t o = ((size_t)b * a.V + v) * a.N + col;
-            if (a.y) *reinterpret_cast<__nv_bfloat162*>(a.y + o) = __floats2bfloat162_rn(r0, r1);
-            if (a.yf) {
-                a.yf[o] = r0;
-                a.yf[o + 1] = r1;
+        for (int mt = 0; mt < MT; ++mt) {
+#pragma unroll
+            for (int h = 0; h < 2; ++h) {
+                const int v = v0 + warp * 16 * MT + mt * 16 + g + 8 * h;
+                if (v >= a.V) continue;
+                float r0 = acc[mt][nt][2 * h] + b0, r1 = acc[mt][nt][2 * h + 1] + b1;
+                if (a.relu) {
+                    r0 = fmaxf(r0, 0.0f);
+                    r1 = fmaxf(r1, 0.0f);
+                }
+                const size_t o = ((size_t)b * a.V + v) * a.N + col;
+                if (a.y) *reinterpret_cast<__nv_bfloat162*>(a.y + o) = __floats2bfloat162_rn(r0, r1);
+                if (a.yf) {
+                    a.yf[o] = r0;
+                    a.yf[o + 1] = r1;
+                }
             }
         }
     }
@@ -512,8 +563,13 @@ int sg_conv3d(const void* x, const void* w, const float* bias, void* y, float* y
         return MP_EINVAL;
     }
     ConvArgs a{(const bf16*)x, (const bf16*)w, bias, (bf16*)y, yf, D, H, W, D * H * W, K, N, sign, relu != 0};
-    dim3 grid((a.V + kCM - 1) / kCM, (N + kCN - 1) / kCN, B);
-    k_conv<<<grid, kCThreads, 0, (cudaStream_t)stream>>>(a);
+    if (N <= 32) {
+        dim3 grid((a.V + 255) / 256, 1, B);
+        k_conv<2, 4><<<grid, kCThreads, 0, (cudaStream_t)stream>>>(a);
+    } else {
+        dim3 grid((a.V + 127) / 128, (N + 63) / 64, B);
+        k_conv<1, 8><<<grid, kCThreads, 0, (cudaStream_t)stream>>>(a);
+    }
     MP_CUDA(cudaGetLastError());
     return MP_OK;
 }
