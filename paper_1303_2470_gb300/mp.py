@@ -128,6 +128,26 @@ def _addr(buf):
     return int(buf)
 
 
+def _check_dev_f32(buf, n, name):
+    """A device FP32 buffer that must hold n values (None allowed). Torch tensors are
+    checked (CUDA, float32, contiguous, at least n values), so that a wrong buffer raises
+    here instead of being read or written out of bounds by the kernels; an integer address
+    is the caller's responsibility."""
+    if buf is not None and hasattr(buf, "numel") and hasattr(buf, "dtype"):
+        if (not getattr(buf, "is_cuda", False) or str(buf.dtype) != "torch.float32" or not buf.is_contiguous()
+                or buf.numel() < n):
+            raise ValueError(f"{name}: needs a contiguous CUDA float32 tensor of at least {n} values, got "
+                             f"shape {tuple(buf.shape)}, {buf.dtype}, on {getattr(buf, 'device', '?')}")
+
+
+def _host_f64(a, n, name):
+    """A host numpy float64 array of exactly n values that the library may read or write
+    in place (C-contiguous)."""
+    if not (isinstance(a, np.ndarray) and a.dtype == np.float64 and a.flags.c_contiguous and a.size == n):
+        raise ValueError(f"{name}: needs a C-contiguous float64 numpy array of {n} values")
+    return a.ctypes.data_as(_dp)
+
+
 def _stream(stream):
     if stream is None:
         return None
@@ -140,7 +160,9 @@ def make_geometry(solid):
     """mp_geometry for a solid mask: a numpy (host) or CUDA tensor (device) uint8 array
     shaped (nz, ny, nx). Returns (struct, keep-alive object)."""
     if hasattr(solid, "data_ptr") and getattr(solid, "is_cuda", False):
-        assert solid.dtype.itemsize == 1 if hasattr(solid.dtype, "itemsize") else True
+        if len(solid.shape) != 3 or str(solid.dtype) not in ("torch.uint8", "torch.bool"):
+            raise ValueError(f"solid: needs a (nz, ny, nx) uint8 or bool tensor, got shape {tuple(solid.shape)}, "
+                             f"{solid.dtype}")
         nz, ny, nx = solid.shape
         t = solid.contiguous()
         return mp_geometry(nx, ny, nz, t.data_ptr(), MP_DEVICE), t
@@ -205,6 +227,7 @@ def mp_init_batch(solid, u, D_b, k_a, k_d, **options) -> Context:
     if not (Db.shape == ka.shape == kd.shape and Db.ndim == 1):
         raise ValueError("D_b, k_a, k_d must be 1-D arrays of equal length")
     o = _options(**options)
+    _check_dev_f32(u, 3 * g.nx * g.ny * g.nz, "u")
     out = _c_vp()
     _check(_lib.mp_init_batch(ctypes.byref(out), ctypes.byref(g), _addr(u), len(Db),
                               Db.ctypes.data_as(_dp), ka.ctypes.data_as(_dp), kd.ctypes.data_as(_dp),
@@ -232,8 +255,9 @@ def mp_vacf(ctx: Context, species: int = 0, direction: int = 0, cap: int | None 
 def mp_vacf_into(ctx: Context, species: int, direction: int, Z: np.ndarray, D: np.ndarray) -> int:
     """mp_vacf into caller-owned host arrays (e.g. pinned); returns the time points available."""
     n = _c_i64()
-    _check(_lib.mp_vacf(ctx.ptr, species, direction, Z.ctypes.data_as(_dp), D.ctypes.data_as(_dp),
-                        min(Z.size, D.size), ctypes.byref(n)))
+    m = min(Z.size, D.size)
+    _check(_lib.mp_vacf(ctx.ptr, species, direction, _host_f64(Z[:m], m, "Z"), _host_f64(D[:m], m, "D"), m,
+                        ctypes.byref(n)))
     return n.value
 
 
@@ -258,10 +282,11 @@ def mp_get_field(ctx: Context, species: int = 0, field: int = 0):
 
 
 def mp_set_field(ctx: Context, species: int, field: int, free, ads=None):
+    n = int(np.prod(ctx.shape))
     fr = np.ascontiguousarray(free, dtype=np.float64)
     ad = None if ads is None else np.ascontiguousarray(ads, dtype=np.float64)
-    _check(_lib.mp_set_field(ctx.ptr, species, field, fr.ctypes.data_as(_dp),
-                             ad.ctypes.data_as(_dp) if ad is not None else None))
+    _check(_lib.mp_set_field(ctx.ptr, species, field, _host_f64(fr, n, "free"),
+                             _host_f64(ad, n, "ads") if ad is not None else None))
 
 
 def mp_classify(solid, stream=None):
@@ -336,12 +361,19 @@ def lb_steady(solid, force, u_out, tau=1.0, tol=1e-7, max_steps=1_000_000, check
     rho_init and rho_out of N values. Returns (steps, residual, converged)."""
     g, keep = make_geometry(solid)
     F = np.ascontiguousarray(force, dtype=np.float64)
+    if F.shape != (3,):
+        raise ValueError("force: needs three components")
+    N = g.nx * g.ny * g.nz
+    if u_out is None:
+        raise ValueError("u_out: a device FP32 buffer of 3*N values is required")
+    bufs = ((u_init, 3 * N, "u_init"), (rho_init, N, "rho_init"), (u_out, 3 * N, "u_out"), (rho_out, N, "rho_out"))
+    for buf, n, name in bufs:
+        _check_dev_f32(buf, n, name)
     steps = _c_i64()
     res = _c_dbl()
     rc = _lib.lb_steady(ctypes.byref(g), F.ctypes.data_as(_dp), float(tau), float(tol), int(max_steps),
-                        int(check_every), _addr(u_init), _addr(rho_init), _addr(u_out), _addr(rho_out),
-                        ctypes.byref(steps),
-                        ctypes.byref(res), _stream(stream))
+                        int(check_every), *(_addr(b[0]) for b in bufs), ctypes.byref(steps), ctypes.byref(res),
+                        _stream(stream))
     del keep
     if rc == MP_ENOTCONVERGED and not raise_on_unconverged:
         return steps.value, res.value, False
