@@ -13,7 +13,7 @@
  * Lattice units: dx = dt = 1. D3Q19 velocities (Sec. "Algorithm": the LB distribution is
  * "discretized over 19 values"); the weights are the standard D3Q19 constants.
  *
- * Readings of the paper taken here (each one is also listed in the design notes):
+ * Readings of the paper taken here:
  *  R1  Eq. (newP) as printed adds desorbed mass back into P but never removes the adsorbed
  *      share P*p_a from P, so total mass would grow. At interfacial nodes the adsorption
  *      event competes with the moves: the stay fraction is 1 - sum_i p_i - p_a.
