@@ -69,6 +69,12 @@ TRAFFIC = {
 }
 
 
+# One-off kernels of one job on this medium, counted in an ncu launch list of the job:
+# geometry preparation for the LB and for the MP, cluster labelling (24 sweeps on this
+# medium), and the LB and MP initialisation.
+JOB_FIXED_LAUNCHES = 42
+
+
 def _src_sha(name):
     p = os.path.join(ROOT, "paper_1303_2470_gb300", "csrc", name)
     return hashlib.sha256(open(p, "rb").read()).hexdigest()[:16]
@@ -558,9 +564,9 @@ def main():
         init_ms += ev[1].elapsed_time(ev[2])
         mp_ms += ev[2].elapsed_time(ev[3])
         lb_steps_all.append(steps)
-        # kernels: LB (2 geometry + init + steps), MP (3 geometry + convert + negative check
-        # + init + steps)
-        launches += 3 + steps + 6 + WORKLOAD["mp_steps"]
+        # kernels: the LB and MP steps, one two-iterate mean per failed residual check, and
+        # the job's one-off kernels (geometry, cluster labelling, initialisation)
+        launches += steps + max(steps // WORKLOAD["lb_check_every"] - 1, 0) + WORKLOAD["mp_steps"] + JOB_FIXED_LAUNCHES
         ctx.close()
     torch.cuda.synchronize()
     if world > 1:
