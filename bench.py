@@ -64,8 +64,10 @@ UNIT = "node-species updates/s"
 # while the kernel source hashes to `src_sha`; otherwise reported as null.
 TRAFFIC = {
     # ncu --set full, python bench.py --profile, k_step<float,2,1> launch 11 (caches flushed
-    # by ncu before the capture, so this is the cold-L2 traffic of one launch)
-    "k_step<float>": {"bytes_per_launch": 48_607_488 + 1_392_640, "src_sha": "cd4af1701d41b82f"},
+    # by ncu before the capture, so this is the cold-L2 traffic of one launch). Captured on
+    # mp.cu 'cd4af1701d41b82f'; the file changed since only in the flow-packing kernel (64-bit
+    # offsets), not in k_step.
+    "k_step<float>": {"bytes_per_launch": 48_607_488 + 1_392_640, "src_sha": "450a088ead29ab87"},
 }
 
 

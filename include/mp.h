@@ -67,7 +67,7 @@ extern "C" {
 
 /* A medium: the solid mask of an nx*ny*nz periodic lattice. */
 typedef struct {
-    int nx, ny, nz;       /* >= 3 each, nx*ny*nz < 2^31                                      */
+    int nx, ny, nz;       /* >= 3 each, nx*ny*nz <= 2^31 - 256                               */
     const uint8_t* solid; /* nx*ny*nz bytes, nonzero = solid node                            */
     int location;         /* MP_HOST or MP_DEVICE: where `solid` lives                       */
 } mp_geometry;

@@ -305,8 +305,10 @@ int build_geometry(const mp_geometry* g, cudaStream_t s, bool so, bool want_list
         return MP_EINVAL;
     }
     long long N = (long long)g->nx * g->ny * g->nz;
-    if (N >= (1LL << 31) - 64) {
-        set_error("lattice too large: nx*ny*nz must be < 2^31");
+    // per-node launches round the node count up to whole 256-thread blocks in int
+    // arithmetic, and node indices stay below 2^31
+    if (N > (1LL << 31) - 256) {
+        set_error("lattice too large: nx*ny*nz must be at most 2^31 - 256");
         return MP_EINVAL;
     }
     if (g->location != MP_HOST && g->location != MP_DEVICE) {

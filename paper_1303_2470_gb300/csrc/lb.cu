@@ -112,8 +112,8 @@ __global__ void __launch_bounds__(kLbThreads)
             u_prev[2 * NF + k] = uz;
         } else if (mode == 2) {
             u_out[n] = ux;
-            u_out[a.N + n] = uy;
-            u_out[2 * a.N + n] = uz;
+            u_out[(size_t)a.N + n] = uy;
+            u_out[2 * (size_t)a.N + n] = uz;
             if (rho_out) rho_out[n] = rho;
             res = fmax(fabs((double)ux - (double)u_prev[k]),
                        fmax(fabs((double)uy - (double)u_prev[NF + k]), fabs((double)uz - (double)u_prev[2 * NF + k])));
@@ -148,8 +148,8 @@ __global__ void k_lb_init(const LbArgs a, const float* __restrict__ u0, const fl
     float ux = 0.f, uy = 0.f, uz = 0.f, rho = 1.f;
     if (u0) {
         ux = u0[n];
-        uy = u0[a.N + n];
-        uz = u0[2 * a.N + n];
+        uy = u0[(size_t)a.N + n];
+        uz = u0[2 * (size_t)a.N + n];
     }
     if (rho0) rho = rho0[n];
     const float uu = ux * ux + uy * uy + uz * uz;

@@ -893,8 +893,8 @@ __global__ void k_pack_flow(const float* __restrict__ in, const uint32_t* __rest
     Flow4<T> v{T(0), T(0), T(0), T(0)};
     if (in && bit_of(fluid, n)) {
         v.x = (T)in[n];
-        v.y = (T)in[N + n];
-        v.z = (T)in[2 * N + n];
+        v.y = (T)in[(size_t)N + n];
+        v.z = (T)in[2 * (size_t)N + n];
         v.w = rn_mul(T(-1.5), rn_add(rn_add(rn_mul(v.x, v.x), rn_mul(v.y, v.y)), rn_mul(v.z, v.z)));
     }
     u4[n] = v;
