@@ -49,6 +49,47 @@ def test_slit_poiseuille_is_the_discrete_stokes_solution():
         assert np.allclose(u[:, 0], 0) and np.allclose(u[:, H + 1], 0)
 
 
+def _duct(H):
+    s = np.zeros((H + 2, H + 2, 3), np.uint8)   # square duct along x: walls at y, z = 0, H + 1
+    s[0] = s[H + 1] = 1
+    s[:, 0] = s[:, H + 1] = 1
+    return s
+
+
+def _duct_series(H, F, nu, terms=401):
+    """Continuum Poiseuille flow in a square duct of side H with the walls half way between
+    the solid and the first fluid nodes: nu lap u = -F, u = 0 on the walls, as the double
+    sine series u = sum_{m,n odd} 16 F H^2 / (nu pi^4 m n (m^2 + n^2)) sin(m pi Y/H)
+    sin(n pi Z/H) at the fluid nodes Y, Z = j - 1/2, j = 1..H. Returns u[Z, Y]."""
+    Y = np.arange(1, H + 1) - 0.5
+    m = np.arange(1, terms + 1, 2)
+    sm = np.sin(np.outer(m, Y) * np.pi / H)
+    A = 16 * F * H ** 2 / (nu * np.pi ** 4 * np.outer(m, m) * (m[:, None] ** 2 + m[None, :] ** 2))
+    return np.einsum("mn,my,nz->zy", A, sm, sm)
+
+
+def test_square_duct_converges_to_the_continuum_series():
+    """Walls normal to y and z at once (the slit test only has z-walls): the steady flow
+    keeps the duct's symmetries exactly and approaches the continuum series at second order
+    in the resolution (halfway bounce-back), |error| / u_max below 0.6 / H^2."""
+    nu, errs = 1.0 / 6.0, {}
+    for H in (12, 24):
+        F = 0.01 * nu / (0.0737 * H * H)             # u_max ~ 0.01 (square duct: 0.0737 F H^2 / nu)
+        u, steps, res, conv = oracle.lb_steady(_duct(H), (F, 0, 0), 1.0, 1e-14, 400000, 100)
+        assert conv
+        ux = u[0, 1:H + 1, 1:H + 1, 1]
+        scale = np.abs(ux).max()
+        assert np.max(np.abs(ux - ux.T)) < 1e-12 * scale                   # y <-> z
+        assert np.max(np.abs(ux - ux[::-1, :])) < 1e-12 * scale            # z -> H + 1 - z
+        assert np.max(np.abs(ux - ux[:, ::-1])) < 1e-12 * scale            # y -> H + 1 - y
+        assert np.max(np.abs(u[0] - u[0, :, :, :1])) < 1e-13               # invariant along x
+        assert np.abs(u[1:]).max() < 1e-4 * scale
+        ref = _duct_series(H, F, nu)
+        errs[H] = np.max(np.abs(ux - ref)) / ref.max()
+        assert errs[H] < 0.6 / H ** 2
+    assert errs[12] / errs[24] > 3.0
+
+
 def test_steady_criterion_and_step_budget():
     """lb_steady stops at the first checked step whose residual max|u(t) - u(t-1)| is
     below tol (a multiple of check_every), and reports non-convergence at max_steps."""
