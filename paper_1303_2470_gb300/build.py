@@ -43,7 +43,7 @@ def build(force: bool = False, verbose: bool = False, ptxas_info: bool = False) 
     nvcc = _nvcc()
     bdir = os.path.join(HERE, "_build")
     os.makedirs(bdir, exist_ok=True)
-    headers = glob.glob(os.path.join(HERE, "csrc", "*.cuh")) + [os.path.join(ROOT, "include", "mp.h")]
+    headers = glob.glob(os.path.join(HERE, "csrc", "*.cuh")) + glob.glob(os.path.join(ROOT, "include", "*.h"))
     srcs = sources()
     objs = [os.path.join(bdir, os.path.basename(s)[:-3] + ".o") for s in srcs]
     extra = ["-Xptxas", "-v"] if ptxas_info else []
