@@ -438,7 +438,15 @@ def run_profile_surrogate():
     return 0
 
 
-def run_profile_case():
+def scheme_options(args):
+    """mp_init options of the MP step's evaluation: the scheme, and for the direct scheme
+    the autotuner or a fixed kernel variant."""
+    if args.scheme == "flux" or args.precision == "fp16":
+        return {"scheme": "flux"}
+    return {"scheme": "direct", "autotune": args.variant < 0, "variant": max(args.variant, 0)}
+
+
+def run_profile_case(args):
     """The workload's kernels on the same 128^3 medium, briefly, for ncu --set full
     captures (python bench.py --profile): LB launches 1-30, k_init, MP launches 1-20."""
     import torch
@@ -449,10 +457,11 @@ def run_profile_case():
     sd = torch.as_tensor(solid).cuda()
     u = torch.zeros((3,) + solid.shape, dtype=torch.float32, device="cuda")
     mp.lb_steady(sd, (1.83e-3, 0, 0), u, tau=WORKLOAD["tau"], tol=0.0, max_steps=30, check_every=30)
-    ctx = mp.mp_init(sd, u, WORKLOAD["D_b"], WORKLOAD["k_a"], WORKLOAD["k_d"], allow_negative=True, capacity=64)
+    ctx = mp.mp_init(sd, u, WORKLOAD["D_b"], WORKLOAD["k_a"], WORKLOAD["k_d"], allow_negative=True, capacity=64,
+                     **scheme_options(args))
     mp.mp_step(ctx, 20)
     torch.cuda.synchronize()
-    print(json.dumps({"profile_case": "ok", "n_fluid": mp.mp_info(ctx)["n_fluid"]}))
+    print(json.dumps({"profile_case": "ok", "n_fluid": mp.mp_info(ctx)["n_fluid"], "variant": mp.mp_variant(ctx)}))
     ctx.close()
     return 0
 
@@ -476,6 +485,12 @@ def main():
                     help="short grouped run (96^3 and 128^3 media x 16 species) for ncu captures")
     ap.add_argument("--profile-surrogate", action="store_true",
                     help="two forward passes of the warm-start network on a 128^3 box for ncu captures")
+    ap.add_argument("--scheme", default="direct", choices=["direct", "flux"],
+                    help="evaluation of the MP step: direct (the paper's form with per-node link "
+                         "tables, default) or flux (exactly antisymmetric link fluxes)")
+    ap.add_argument("--variant", type=int, default=-1,
+                    help="direct scheme: MP_VARIANT_* flags of a fixed kernel variant, or -1 (default) "
+                         "to let mp_init autotune it")
     ap.add_argument("--profile", action="store_true",
                     help="short run of the same medium and kernels for ncu captures: 30 LB steps, "
                          "mp_init and 20 MP steps, no timing")
@@ -484,7 +499,7 @@ def main():
     if args.impl == "reference":
         return run_reference(args)
     if args.profile:
-        return run_profile_case()
+        return run_profile_case(args)
     if args.profile_batched:
         return run_profile_batched()
     if args.profile_surrogate:
@@ -535,14 +550,15 @@ def main():
                                         stream=stream)
         ev[1].record(stream)
         ctx = mp.mp_init(solid_arg, u, WORKLOAD["D_b"], WORKLOAD["k_a"], WORKLOAD["k_d"],
-                         capacity=WORKLOAD["mp_steps"] + 2, stream=stream, allow_negative=True,
-                         precision=args.precision)
+                         capacity=WORKLOAD["mp_steps"] + 26, stream=stream, allow_negative=True,
+                         precision=args.precision, **scheme_options(args))
         ev[2].record(stream)
         mp.mp_step(ctx, WORKLOAD["mp_steps"])
         if host_out is not None:
             mp.mp_vacf_into(ctx, 0, 0, host_out[0], host_out[1])
         ev[3].record(stream)
         info = mp.mp_info(ctx)
+        info["variant"] = mp.mp_variant(ctx)
         return steps, res, conv, info, ev, ctx
 
     for _ in range(args.warmup):
@@ -597,7 +613,13 @@ def main():
     n_iface = int(info["n_interface"])
     S = WORKLOAD["species"]
     eb = 2 if args.precision == "fp16" else 4                     # bytes per stored field value
-    mp_name = "k_step<float,half>" if args.precision == "fp16" else "k_step<float>"
+    variant = info["variant"]
+    if variant == "flux":
+        mp_name, mp_src = ("k_step<float,half>" if args.precision == "fp16" else "k_step<float>"), "mp.cu"
+    else:
+        # a persistent launch runs the whole run of steps: its per-step time is the unit
+        mp_name = "k_direct_persistent" if variant.startswith("persistent") else "k_direct_step"
+        mp_src = "mp_direct.cu"
     # per MP launch: 2 fields read + written per fluid node and species, flow 12 B + flags 1 B
     # per fluid node, the adsorbed partners' 2 fields read + written per interfacial node
     mp_bytes = n_fluid * (4 * eb * S + 13) + n_iface * 4 * eb * S
@@ -608,7 +630,7 @@ def main():
     kern = {
         mp_name: {"share": mp_ms / total_ms, "avg_launch_us": mp_launch_s * 1e6,
                           "algorithmic_bytes": mp_bytes, "gbs": mp_bytes / mp_launch_s / 1e9,
-                          "src": "mp.cu"},
+                          "src": mp_src, "variant": variant},
         "k_lb_step": {"share": lb_ms / total_ms, "avg_launch_us": lb_launch_s * 1e6,
                       "algorithmic_bytes": lb_bytes, "gbs": lb_bytes / lb_launch_s / 1e9, "src": "lb.cu"},
     }

@@ -65,6 +65,21 @@ extern "C" {
 
 #define MP_MAX_SPECIES 32 /* species (D_b, k_a, k_d sets) sharing one medium and flow      */
 
+/* ---- evaluation of the step (mp_options.scheme) --------------------------------------- */
+/* X + the sum of exactly antisymmetric net link fluxes, every product correctly rounded, so
+ * that both ends of a link see opposite fluxes: total mass changes only by the final rounding
+ * of each node's update (and not at all for a stationary field). FP64, FP32 and FP16. */
+#define MP_SCHEME_FLUX 0
+/* The paper's direct form X' = sum_i p_i(r - c_i) X(r - c_i) + (1 - sum_i p_i(r) - p_a) X(r)
+ * + p_d X_a (Eq. propagated_quantity with Eqs. Pads, newP), with the incoming link
+ * probabilities (one species) or their flow-dependent parts (several species), the
+ * outgoing sums and u*_g of every fluid node tabulated once by mp_init (about 80 bytes per
+ * fluid node). FP32 only. Link probabilities are bitwise those of MP_SCHEME_FLUX; total mass
+ * is conserved up to the FP32 rounding of each node's outgoing sum (a relative error below
+ * 2^-25 of X(r) per step, of random sign across the nodes of a porous medium; in media with
+ * few distinct nodes, such as slits, it adds up coherently). */
+#define MP_SCHEME_DIRECT 1
+
 /* A medium: the solid mask of an nx*ny*nz periodic lattice. */
 typedef struct {
     int nx, ny, nz;       /* >= 3 each, nx*ny*nz <= 2^31 - 256                               */
@@ -85,7 +100,22 @@ typedef struct {
                            0 means 131072. mp_step fails once the series is full.           */
     void* stream;       /* cudaStream_t of all work of the context; NULL = default stream   */
     int rounding;       /* MP_FP16 only: MP_ROUND_STOCHASTIC (default) or MP_ROUND_NEAREST  */
+    int scheme;         /* MP_SCHEME_FLUX (default) or MP_SCHEME_DIRECT                      */
+    int autotune;       /* MP_SCHEME_DIRECT only. 0: run the variant given below. Nonzero:
+                           mp_init times every variant (link table or link terms recomputed
+                           from the flow; one launch per step or one persistent launch per run
+                           of steps; blocks of 128, 256 or 512) for 20 steps on the initial
+                           state, restores the state and keeps the fastest (needs 24 free
+                           entries in the series). See mp_variant.                          */
+    int variant;        /* MP_SCHEME_DIRECT without autotune: 0 (one launch per step, link
+                           table, blocks of 256) or MP_VARIANT_* flags                       */
 } mp_options;
+
+/* ---- kernel variants of MP_SCHEME_DIRECT (mp_options.variant); all give the same fields ---- */
+#define MP_VARIANT_RECOMPUTE 1  /* link terms recomputed from the packed flow, no link table   */
+#define MP_VARIANT_PERSISTENT 2 /* one persistent launch per run of steps                       */
+#define MP_VARIANT_BLOCK128 4   /* blocks of 128 threads (default 256)                          */
+#define MP_VARIANT_BLOCK512 8   /* blocks of 512 threads                                        */
 
 void mp_default_options(mp_options* opt);
 
@@ -136,6 +166,8 @@ int mp_init_batch(mp_ctx** out, const mp_geometry* g, const float* u, int n_spec
  * legacy or per-thread default stream), calls with n >= 128 replay runs of 64 steps from a
  * CUDA graph captured at first use (one per starting buffer): the same kernels with the
  * same arguments, so results are identical; it only removes the per-launch host cost.
+ * With MP_SCHEME_DIRECT the variant chosen at mp_init runs (see mp_variant); a persistent
+ * variant runs up to 2^20 steps per launch.
  * Errors: MP_EINVAL (n < 0, or the series would exceed its capacity), MP_ECUDA.
  */
 int mp_step(mp_ctx* c, int64_t n);
@@ -207,12 +239,17 @@ int mp_set_field(mp_ctx* c, int species, int field, const double* free_dense,
  * mp_group_step advances every context n steps (same results as separate mp_step calls:
  * identical fields; Z and D equal up to the order of the FP64 block sums when the block
  * size differs from 256). mp_group_block_size returns the block size in use.
+ * Contexts created with MP_SCHEME_DIRECT form a direct group (all of them must be): one
+ * launch per step or one persistent launch per run of steps for all of them, the variant
+ * autotuned as for mp_options.autotune when `autotune` is nonzero (graph_steps is then
+ * unused: runs of 128 steps or more replay graphs of 64); mp_group_variant names it.
  * Errors: MP_EINVAL, MP_ENOMEM, MP_ECUDA.
  */
 typedef struct mp_group mp_group;
 int mp_group_create(mp_group** out, mp_ctx* const* ctxs, int n, int graph_steps, int autotune);
 int mp_group_step(mp_group* g, int64_t n);
 int mp_group_block_size(mp_group* g);
+const char* mp_group_variant(mp_group* g);
 void mp_group_free(mp_group* g);
 
 /*
@@ -254,11 +291,14 @@ int mp_classify(const mp_geometry* g, uint8_t* cls, int64_t* n_fluid, int64_t* n
  *  X, X_ads      device, FP32, N each: the field and its adsorbed partner (dense; X_ads is
  *                read on interfacial nodes only).
  *  X_out, X_ads_out  device, FP32, N each, written everywhere (zero on solid nodes, X_ads_out
- *                zero off the interface); must not alias the inputs.
+ *                zero off the interface); no byte of either may lie in X, X_ads, solid, u,
+ *                Z_out or the other output (MP_EINVAL otherwise).
  *  Z_out         device, one double, written when the step completes.
  *  stream        cudaStream_t or NULL. Asynchronous.
- * The first call on a device looks up the scratch array's device address (once, with that
- * device current); make that first call before any stream capture. Every call shares the
+ * The first call on a device looks up the scratch array's device address (with that device
+ * current) and remembers it with the id of the device's context; make that first call before
+ * any stream capture. After a cudaDeviceReset the next call finds a new context and looks the
+ * address up again (so it is again a first call). Every call shares the
  * one scratch array and leaves its contents behind: the counter is cleared by each call, so
  * calls that overlap on the GPU (different streams, concurrent host threads) race and must
  * be serialised by the caller.
@@ -267,6 +307,31 @@ int mp_classify(const mp_geometry* g, uint8_t* cls, int64_t* n_fluid, int64_t* n
 int mp_step_noalloc(int nx, int ny, int nz, const uint8_t* solid, const float* u, double D_b,
                     double k_a, double k_d, int direction, const float* X, const float* X_ads,
                     float* X_out, float* X_ads_out, double* Z_out, void* stream);
+
+/*
+ * mp_variant -- text naming how mp_step runs the context (no counterpart in the paper):
+ * "flux" for MP_SCHEME_FLUX; for MP_SCHEME_DIRECT the launch form ("per-step" or
+ * "persistent"), the link terms ("table" or "recompute") and the block size. Valid until the
+ * context is freed.
+ *
+ * A persistent launch runs many steps with a device-wide barrier between them. Every wait
+ * at that barrier is bounded (2 s); a wait that gives up makes the launch return early, and
+ * the next call that synchronises the context (mp_vacf, mp_mass, mp_get_field) fails with
+ * MP_ETIMEOUT: the fields and series written after the failed step are then not valid.
+ */
+const char* mp_variant(mp_ctx* c);
+
+/*
+ * mp_grid_wait_selftest -- runs the bounded device-wide barrier of the persistent step on its
+ * own (no counterpart in the paper): n_blocks co-resident blocks of 32 threads meet at
+ * `rounds` barriers. With `unreachable` nonzero every barrier waits for one block more than
+ * the grid holds (an arrival that never comes), so each wait must give up after timeout_ns
+ * nanoseconds; the call then returns MP_ETIMEOUT and the device stays usable.
+ *  stream   cudaStream_t or NULL; synchronised before return.
+ * Errors: MP_EINVAL (more blocks than can be resident at once, rounds outside 1..1e6,
+ * timeout_ns outside 0..1e10), MP_ECUDA, MP_ETIMEOUT.
+ */
+int mp_grid_wait_selftest(int n_blocks, int rounds, int unreachable, int64_t timeout_ns, void* stream);
 
 /* mp_free -- release a context and all its device memory (NULL is accepted). */
 void mp_free(mp_ctx* c);

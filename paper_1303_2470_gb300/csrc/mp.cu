@@ -30,7 +30,9 @@
 #include <cuda_fp16.h>
 
 #include "internal.cuh"
+#include "lattice.cuh"
 #include "link_arith.cuh"
+#include "mp_ctx.cuh"
 
 namespace mp {
 const char* last_error_text();
@@ -44,62 +46,6 @@ constexpr int kThreads = 256;
 constexpr int kWarps = kThreads / 32;
 constexpr int kMaxF = 4;  // density + up to three velocity moments
 constexpr uint32_t kAllLinks = (1u << 18) - 1u;
-
-// (u_x, u_y, u_z, -3/2 |u|^2) of one node, loaded as one vector
-template <typename T>
-struct alignas(4 * sizeof(T)) Flow4 {
-    T x, y, z, w;
-};
-
-// exact quotient n / d for 0 <= n < 2^31, 2 <= d < 2^31, with m = floor(2^32 / d): the
-// estimate umulhi(n, m) is floor(n/d) or one less
-struct Div {
-    unsigned d, m;
-};
-Div make_div(unsigned d) { return Div{d, (unsigned)((1ull << 32) / d)}; }
-__device__ __forceinline__ unsigned divq(unsigned n, Div v)
-{
-    unsigned q = __umulhi(n, v.m);
-    if (n - q * v.d >= v.d) ++q;
-    return q;
-}
-
-// all propagated fields of one node and species, stored together (padded to 2 or 4)
-template <typename T, int FP>
-struct alignas(FP * sizeof(T)) FieldVec {
-    T v[FP];
-};
-
-// 32-byte records of eight FP32 values move as one 256-bit access (ld/st.global.v8.f32):
-// with records scattered over the fluid list, two 16-byte halves would each cost a full
-// L1 sector request per lane
-template <typename T, int W>
-__device__ __forceinline__ FieldVec<T, W> ld_rec(const FieldVec<T, W>* p)
-{
-    return *p;
-}
-template <>
-__device__ __forceinline__ FieldVec<float, 8> ld_rec<float, 8>(const FieldVec<float, 8>* p)
-{
-    FieldVec<float, 8> r;
-    asm("ld.global.v8.f32 {%0,%1,%2,%3,%4,%5,%6,%7}, [%8];"
-        : "=f"(r.v[0]), "=f"(r.v[1]), "=f"(r.v[2]), "=f"(r.v[3]), "=f"(r.v[4]), "=f"(r.v[5]), "=f"(r.v[6]),
-          "=f"(r.v[7])
-        : "l"(p));
-    return r;
-}
-template <typename T, int W>
-__device__ __forceinline__ void st_rec(FieldVec<T, W>* p, const FieldVec<T, W>& r)
-{
-    *p = r;
-}
-template <>
-__device__ __forceinline__ void st_rec<float, 8>(FieldVec<float, 8>* p, const FieldVec<float, 8>& r)
-{
-    asm volatile("st.global.v8.f32 [%0], {%1,%2,%3,%4,%5,%6,%7,%8};" ::"l"(p), "f"(r.v[0]), "f"(r.v[1]), "f"(r.v[2]),
-                 "f"(r.v[3]), "f"(r.v[4]), "f"(r.v[5]), "f"(r.v[6]), "f"(r.v[7])
-                 : "memory");
-}
 
 // ---------------------------------------------------------------------------------------
 // Storage type TS of the fields: float or double (the arithmetic type T itself), or IEEE
@@ -242,35 +188,10 @@ __device__ __forceinline__ T pick(const T v[3], int g)
     return g == 0 ? v[0] : (g == 1 ? v[1] : v[2]);
 }
 
-// Periodic neighbourhood of a node: offsets to x-1, x+1, y-1, y+1, z-1, z+1.
-struct Nbr {
-    int n, oxm, oxp, oym, oyp, ozm, ozp;
-};
-
 template <typename T>
 __device__ __forceinline__ Nbr node_nbrs(const Args<T>& a, int n)
 {
-    Nbr b;
-    const int yz = (int)divq((unsigned)n, a.dx);
-    const int x = n - yz * a.nx;
-    const int z = (int)divq((unsigned)n, a.dxy);
-    const int y = yz - z * a.ny;
-    const int nxy = a.nx * a.ny;
-    b.n = n;
-    b.oxm = x == 0 ? a.nx - 1 : -1;
-    b.oxp = x == a.nx - 1 ? 1 - a.nx : 1;
-    b.oym = y == 0 ? (a.ny - 1) * a.nx : -a.nx;
-    b.oyp = y == a.ny - 1 ? (1 - a.ny) * a.nx : a.nx;
-    b.ozm = z == 0 ? (a.nz - 1) * nxy : -nxy;
-    b.ozp = z == a.nz - 1 ? (1 - a.nz) * nxy : nxy;
-    return b;
-}
-
-// s_i = r - c_i
-__device__ __forceinline__ int src_of(const Nbr& b, int i)
-{
-    return b.n + (cx(i) > 0 ? b.oxm : (cx(i) < 0 ? b.oxp : 0)) + (cy(i) > 0 ? b.oym : (cy(i) < 0 ? b.oyp : 0)) +
-           (cz(i) > 0 ? b.ozm : (cz(i) < 0 ? b.ozp : 0));
+    return nbrs_of(a.nx, a.ny, a.nz, a.dx, a.dxy, n);
 }
 
 // What a fluid node r needs from its links. Link i is the inflow direction c_i: its source
@@ -345,14 +266,6 @@ __device__ __forceinline__ void mean_step(const T (&pout)[kQ], int g, T& us, T& 
             us2 += pout[i];
         }
     }
-}
-
-template <typename T>
-__device__ __forceinline__ T warp_sum(T v)
-{
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
-    return v;
 }
 
 // Sum `cnt` per-thread values over the block: warp sums in T (FP32 or FP64), then FP64
@@ -924,39 +837,6 @@ __global__ void k_open_mask(const int32_t* __restrict__ flist, const uint32_t* _
 // ---------------------------------------------------------------------------------------
 // Context and C ABI
 // ---------------------------------------------------------------------------------------
-struct mp_ctx {
-    Geometry geo;
-    int precision = MP_FP32;
-    int S = 0, F = 0, M = 0;
-    int dir[3] = {0, 0, 0};
-    cudaStream_t stream = nullptr;
-    long long cap = 0;
-    long long t = 0;
-    double Db[MP_MAX_SPECIES], ka[MP_MAX_SPECIES], kd[MP_MAX_SPECIES];
-    void* u4 = nullptr;          // Flow4<T> per node
-    uint32_t* fmask = nullptr;   // open-link mask per fluid node
-    void* P[2] = {nullptr, nullptr};
-    void* A[2] = {nullptr, nullptr};
-    int cur = 0;
-    double* Z = nullptr;
-    double* D = nullptr;
-    long long* tdev = nullptr;
-    double* partials = nullptr;
-    unsigned int* ticket = nullptr;
-    int blocks = 0;
-    long long n_neg_links = 0, n_neg_stay = 0;
-    std::vector<int32_t> ilist;
-    size_t elem = 4;
-    int FP = 2;  // fields per species record (F padded to 2 or 4)
-    int SP = 1;  // species padded to whole chunks (1 for one species)
-    int SC = 1;  // species per chunk
-    mp_group* owner = nullptr;  // set while the context steps as part of a group
-    double zsc[MP_MAX_SPECIES] = {};  // stored value x zsc = field value (binary16 storage)
-    int stochastic = 1;               // binary16 rounding: stochastic (1) or to nearest (0)
-    // runs of kCtxGraphSteps steps captured once per starting buffer (cur) and replayed
-    cudaGraph_t graph[2] = {nullptr, nullptr};
-    cudaGraphExec_t exec[2] = {nullptr, nullptr};
-};
 
 namespace {
 
@@ -1006,6 +886,7 @@ Args<T> make_args(const mp_ctx* c)
 void destroy(mp_ctx* c)
 {
     if (!c) return;
+    direct_free(c);
     for (int b = 0; b < 2; ++b) {
         if (c->exec[b]) cudaGraphExecDestroy(c->exec[b]);
         if (c->graph[b]) cudaGraphDestroy(c->graph[b]);
@@ -1200,6 +1081,9 @@ void mp_default_options(mp_options* opt)
     opt->capacity = 131072;
     opt->stream = nullptr;
     opt->rounding = MP_ROUND_STOCHASTIC;
+    opt->scheme = MP_SCHEME_FLUX;
+    opt->autotune = 0;
+    opt->variant = 0;
 }
 
 const char* mp_last_error(void) { return mp::last_error_text(); }
@@ -1223,6 +1107,18 @@ int mp_init_batch(mp_ctx** out, const mp_geometry* g, const float* u, int n_spec
     }
     if (opt.precision != MP_FP32 && opt.precision != MP_FP64 && opt.precision != MP_FP16) {
         set_error("precision must be MP_FP32, MP_FP64 or MP_FP16");
+        return MP_EINVAL;
+    }
+    if (opt.scheme != MP_SCHEME_FLUX && opt.scheme != MP_SCHEME_DIRECT) {
+        set_error("scheme must be MP_SCHEME_FLUX or MP_SCHEME_DIRECT");
+        return MP_EINVAL;
+    }
+    if (opt.variant < 0 || opt.variant > 15 || (opt.variant & 12) == 12) {
+        set_error("variant must combine MP_VARIANT_* flags (one block size at most)");
+        return MP_EINVAL;
+    }
+    if (opt.scheme == MP_SCHEME_DIRECT && opt.precision != MP_FP32) {
+        set_error("MP_SCHEME_DIRECT needs MP_FP32 storage");
         return MP_EINVAL;
     }
     if (opt.rounding != MP_ROUND_STOCHASTIC && opt.rounding != MP_ROUND_NEAREST) {
@@ -1265,6 +1161,7 @@ int mp_init_batch(mp_ctx** out, const mp_geometry* g, const float* u, int n_spec
         return MP_ENOMEM;
     }
     c->precision = opt.precision;
+    c->scheme = opt.scheme;
     c->stochastic = opt.rounding == MP_ROUND_STOCHASTIC;
     c->stream = (cudaStream_t)opt.stream;
     c->cap = opt.capacity;
@@ -1307,6 +1204,7 @@ int mp_init_batch(mp_ctx** out, const mp_geometry* g, const float* u, int n_spec
                   " open links have a negative probability p_i (set allow_negative to accept)");
         rc = MP_ENEGPROB;
     }
+    if (rc == MP_OK && c->scheme == MP_SCHEME_DIRECT) rc = direct_setup(c, opt.autotune, opt.variant);
     if (rc != MP_OK) {
         destroy(c);
         return rc;
@@ -1337,9 +1235,16 @@ int mp_step(mp_ctx* c, int64_t n)
         set_error("the context belongs to a group: step it with mp_group_step");
         return MP_EINVAL;
     }
+    if (c->scheme == MP_SCHEME_DIRECT) return direct_step(c, n);
     return c->precision == MP_FP64   ? step_typed<double, double>(c, n)
            : c->precision == MP_FP16 ? step_typed<float, __half>(c, n)
                                      : step_typed<float, float>(c, n);
+}
+
+const char* mp_variant(mp_ctx* c)
+{
+    if (!c) return "";
+    return c->scheme == MP_SCHEME_DIRECT ? direct_state_variant(c->dstate) : "flux";
 }
 
 int mp_vacf(mp_ctx* c, int species, int direction, double* Z, double* D, int64_t cap, int64_t* n_out)
@@ -1353,6 +1258,7 @@ int mp_vacf(mp_ctx* c, int species, int direction, double* Z, double* D, int64_t
         set_error("species out of range, direction not propagated, or negative cap");
         return MP_EINVAL;
     }
+    if (int rc = direct_check(c)) return rc;
     const long long avail = c->t + 1;
     const long long cnt = cap < avail ? cap : avail;
     const size_t off = (size_t)(species * c->M + m) * c->cap;
@@ -1371,6 +1277,7 @@ int mp_mass(mp_ctx* c, int species, double out[3])
         set_error("species out of range or out is NULL");
         return MP_EINVAL;
     }
+    if (int rc = direct_check(c)) return rc;
     return c->precision == MP_FP64   ? mass_typed<double, double>(c, species, out)
            : c->precision == MP_FP16 ? mass_typed<float, __half>(c, species, out)
                                      : mass_typed<float, float>(c, species, out);
@@ -1403,6 +1310,7 @@ int mp_get_field(mp_ctx* c, int species, int field, double* free_dense, double* 
         set_error("species or field out of range, or free_dense is NULL");
         return MP_EINVAL;
     }
+    if (int rc = direct_check(c)) return rc;
     const size_t N = (size_t)c->geo.N;
     const size_t NI = (size_t)(c->geo.n_iface > 0 ? c->geo.n_iface : 1);
     const size_t FP = (size_t)c->FP, SP = (size_t)c->SP, E = c->elem;
@@ -1492,6 +1400,7 @@ struct mp_group {
     cudaGraph_t graph = nullptr;
     cudaGraphExec_t exec = nullptr;
     int graph_steps = 0;
+    mp::DirectState* direct = nullptr;  // a group of MP_SCHEME_DIRECT contexts
 };
 
 namespace {
@@ -1627,6 +1536,7 @@ void group_destroy(mp_group* g)
 {
     if (!g) return;
     if (g->stream) cudaStreamSynchronize(g->stream);
+    if (g->direct) direct_state_free(g->direct);
     for (mp_ctx* c : g->ctx) c->owner = nullptr;
     if (g->exec) cudaGraphExecDestroy(g->exec);
     if (g->graph) cudaGraphDestroy(g->graph);
@@ -1649,8 +1559,10 @@ int mp_group_create(mp_group** out, mp_ctx* const* ctxs, int n, int graph_steps,
         return MP_EINVAL;
     }
     for (int c = 0; c < n; ++c) {
-        if (!ctxs[c] || ctxs[c]->precision != MP_FP32 || ctxs[c]->owner || ctxs[c]->FP != ctxs[0]->FP) {
-            set_error("mp_group_create: contexts must be distinct, FP32, ungrouped, with the same field layout");
+        if (!ctxs[c] || ctxs[c]->precision != MP_FP32 || ctxs[c]->owner || ctxs[c]->FP != ctxs[0]->FP ||
+            ctxs[c]->scheme != ctxs[0]->scheme) {
+            set_error("mp_group_create: contexts must be distinct, FP32, ungrouped, with the same field layout "
+                      "and scheme");
             return MP_EINVAL;
         }
         for (int d = 0; d < c; ++d)
@@ -1672,6 +1584,18 @@ int mp_group_create(mp_group** out, mp_ctx* const* ctxs, int n, int graph_steps,
     int rc = MP_OK;
     cudaError_t e = cudaStreamCreateWithFlags(&g->stream, cudaStreamNonBlocking);
     if (e == cudaSuccess) e = cudaEventCreateWithFlags(&g->ev, cudaEventDisableTiming);
+    if (e == cudaSuccess && ctxs[0]->scheme == MP_SCHEME_DIRECT) {
+        // a direct group: its own launch state over the contexts, on the group's stream
+        rc = group_sync_in(g);
+        if (rc == MP_OK) rc = direct_state_create(ctxs, n, g->stream, autotune, 0, &g->direct);
+        if (rc != MP_OK) {
+            group_destroy(g);
+            return rc;
+        }
+        for (mp_ctx* c : g->ctx) c->owner = g;
+        *out = g;
+        return MP_OK;
+    }
     if (e == cudaSuccess) e = cudaMalloc(&g->d_args, sizeof(Args<float>) * n);
     if (e == cudaSuccess) e = cudaMalloc(&g->d_ptrs, sizeof(GroupPtrs) * 2 * n);
     if (e == cudaSuccess) {
@@ -1753,6 +1677,10 @@ int mp_group_step(mp_group* g, int64_t n)
             return MP_EINVAL;
         }
     if (int rc = group_sync_in(g)) return rc;
+    if (g->direct) {
+        if (int rc = direct_state_step(g->direct, n)) return rc;
+        return group_sync_out(g);
+    }
     while (n > 0 && g->graph_steps > 0 && g->phase != 0) {
         MP_CUDA(group_launch(g, true));
         --n;
@@ -1775,7 +1703,14 @@ int mp_group_step(mp_group* g, int64_t n)
 
 int mp_group_block_size(mp_group* g)
 {
+    if (g && g->direct) return direct_state_block(g->direct);
     return g ? g->block : 0;
+}
+
+const char* mp_group_variant(mp_group* g)
+{
+    if (!g) return "";
+    return g->direct ? direct_state_variant(g->direct) : "flux";
 }
 
 void mp_group_free(mp_group* g) { group_destroy(g); }

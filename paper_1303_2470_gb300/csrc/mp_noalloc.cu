@@ -131,10 +131,45 @@ __global__ void __launch_bounds__(kNaThreads)
     }
 }
 
-// Device address of the scratch array, looked up once per device (with that device
-// current) and remembered: in host code the array's name is only a host-side stand-in.
+// Device address of the scratch array. In host code the array's name is only a host-side
+// stand-in, so the address is looked up with cudaGetSymbolAddress (with the device current)
+// and remembered per device together with the unique id of the context it belongs to. A
+// cudaDeviceReset ends that context and the next call runs in a new one, whose module copy
+// of the array lives elsewhere: a changed context id triggers a fresh lookup. The driver's
+// context queries are resolved through the runtime, so the library needs no link to libcuda.
+typedef int (*CtxGetCurrentFn)(void**);
+typedef int (*CtxGetIdFn)(void*, unsigned long long*);
+
 std::mutex g_scratch_mu;
-unsigned char* g_scratch_ptr[128] = {};
+struct ScratchSlot {
+    unsigned char* ptr = nullptr;
+    unsigned long long ctx_id = 0;
+};
+ScratchSlot g_scratch[128];
+CtxGetCurrentFn g_ctx_current = nullptr;
+CtxGetIdFn g_ctx_id = nullptr;
+bool g_ctx_fns_tried = false;
+
+// unique id of the calling thread's current context; 0 if none or not available
+unsigned long long current_ctx_id()
+{
+    if (!g_ctx_fns_tried) {
+        g_ctx_fns_tried = true;
+        void* f = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        if (cudaGetDriverEntryPointByVersion("cuCtxGetCurrent", &f, 12000, cudaEnableDefault, &q) == cudaSuccess &&
+            q == cudaDriverEntryPointSuccess)
+            g_ctx_current = reinterpret_cast<CtxGetCurrentFn>(f);
+        f = nullptr;
+        if (cudaGetDriverEntryPointByVersion("cuCtxGetId", &f, 12000, cudaEnableDefault, &q) == cudaSuccess &&
+            q == cudaDriverEntryPointSuccess)
+            g_ctx_id = reinterpret_cast<CtxGetIdFn>(f);
+    }
+    void* ctx = nullptr;
+    unsigned long long id = 0;
+    if (!g_ctx_current || !g_ctx_id || g_ctx_current(&ctx) != 0 || !ctx || g_ctx_id(ctx, &id) != 0) return 0;
+    return id;
+}
 
 int scratch_address(unsigned char** out)
 {
@@ -146,14 +181,25 @@ int scratch_address(unsigned char** out)
         return MP_EINVAL;
     }
     std::lock_guard<std::mutex> lock(g_scratch_mu);
-    if (!g_scratch_ptr[dev]) {
+    ScratchSlot& slot = g_scratch[dev];
+    const unsigned long long id = slot.ptr ? current_ctx_id() : 0;
+    if (!slot.ptr || id == 0 || id != slot.ctx_id) {
         void* p = nullptr;
-        e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
+        e = cudaGetSymbolAddress(&p, g_noalloc_scratch);  // also makes the device's context current
         if (e != cudaSuccess) return cuda_fail(e, "cudaGetSymbolAddress(scratch)");
-        g_scratch_ptr[dev] = static_cast<unsigned char*>(p);
+        slot.ptr = static_cast<unsigned char*>(p);
+        slot.ctx_id = current_ctx_id();
     }
-    *out = g_scratch_ptr[dev];
+    *out = slot.ptr;
     return MP_OK;
+}
+
+// [a, a + na) and [b, b + nb) share a byte (null pointers share nothing)
+bool overlap(const void* a, size_t na, const void* b, size_t nb)
+{
+    if (!a || !b || na == 0 || nb == 0) return false;
+    const uintptr_t x = reinterpret_cast<uintptr_t>(a), y = reinterpret_cast<uintptr_t>(b);
+    return x < y + nb && y < x + na;
 }
 
 }  // namespace
@@ -177,9 +223,20 @@ extern "C" int mp_step_noalloc(int nx, int ny, int nz, const uint8_t* solid, con
         set_error("mp_step_noalloc: solid, X, X_ads, X_out, X_ads_out and Z_out are required");
         return MP_EINVAL;
     }
-    if (X_out == X || X_ads_out == X_ads || X_out == X_ads || X_ads_out == X) {
-        set_error("mp_step_noalloc: the output arrays must not alias the inputs");
-        return MP_EINVAL;
+    {
+        // the step reads neighbours of every node while other threads write their results,
+        // so no output byte may lie in any input (or in the other output)
+        const size_t fb = (size_t)N * sizeof(float);
+        const void* in[5] = {X, X_ads, solid, u, Z_out};
+        const size_t in_b[5] = {fb, fb, (size_t)N, u ? 3 * fb : 0, sizeof(double)};
+        const void* outs[2] = {X_out, X_ads_out};
+        bool bad = overlap(X_out, fb, X_ads_out, fb);
+        for (int o = 0; o < 2; ++o)
+            for (int j = 0; j < 5; ++j) bad = bad || overlap(outs[o], fb, in[j], in_b[j]);
+        if (bad) {
+            set_error("mp_step_noalloc: the output arrays must not overlap the inputs, Z_out or each other");
+            return MP_EINVAL;
+        }
     }
     if (!(D_b > 0.0 && D_b <= 0.25) || !(k_a >= 0.0 && k_a <= 1.0) || !(k_d >= 0.0 && k_d <= 1.0) ||
         direction < -1 || direction > 2) {

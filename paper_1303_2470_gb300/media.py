@@ -110,6 +110,15 @@ def random_flow(solid: np.ndarray, amplitude: float, seed: int) -> np.ndarray:
     return u
 
 
+def drift_flow(solid: np.ndarray, mean: float, amplitude: float, seed: int) -> np.ndarray:
+    """Seeded test flow u[3, ...]: random_flow(solid, amplitude, seed) plus a uniform drift
+    `mean` along x on the fluid nodes (zero on solids), so that the mean fluid velocity is
+    `mean` along x up to the sampling noise. A test input, not a solution of a flow problem."""
+    u = random_flow(solid, amplitude, seed)
+    u[0][solid == 0] += mean
+    return u
+
+
 def species(n: int, seed: int, D_b=(0.01, 0.1), k=(1e-4, 1e-1)):
     """n tracer species: D_b uniform in D_b, k_a and k_d log-uniform in k.
     Returns three float64 arrays (D_b, k_a, k_d)."""

@@ -37,6 +37,12 @@ MP_ROUND_NEAREST = 1
 MP_INIT_EQUILIBRIUM = 0
 MP_INIT_UNIFORM = 1
 MP_MAX_SPECIES = 32
+MP_SCHEME_FLUX = 0
+MP_SCHEME_DIRECT = 1
+MP_VARIANT_RECOMPUTE = 1
+MP_VARIANT_PERSISTENT = 2
+MP_VARIANT_BLOCK128 = 4
+MP_VARIANT_BLOCK512 = 8
 
 _c_int, _c_i64, _c_dbl, _c_vp = ctypes.c_int, ctypes.c_int64, ctypes.c_double, ctypes.c_void_p
 
@@ -47,7 +53,8 @@ class mp_geometry(ctypes.Structure):
 
 class mp_options(ctypes.Structure):
     _fields_ = [("precision", _c_int), ("directions", _c_int), ("init_density", _c_int),
-                ("allow_negative", _c_int), ("capacity", _c_i64), ("stream", _c_vp), ("rounding", _c_int)]
+                ("allow_negative", _c_int), ("capacity", _c_i64), ("stream", _c_vp), ("rounding", _c_int),
+                ("scheme", _c_int), ("autotune", _c_int), ("variant", _c_int)]
 
 
 class mp_info_t(ctypes.Structure):
@@ -83,6 +90,11 @@ _lib.mp_group_step.argtypes = [_c_vp, _c_i64]
 _lib.mp_group_block_size.argtypes = [_c_vp]
 _lib.mp_group_free.argtypes = [_c_vp]
 _lib.mp_group_free.restype = None
+_lib.mp_variant.argtypes = [_c_vp]
+_lib.mp_variant.restype = ctypes.c_char_p
+_lib.mp_group_variant.argtypes = [_c_vp]
+_lib.mp_group_variant.restype = ctypes.c_char_p
+_lib.mp_grid_wait_selftest.argtypes = [_c_int, _c_int, _c_int, _c_i64, _c_vp]
 _f32, _c_i, _vp = ctypes.c_float, _c_int, _c_vp
 _lib.sg_conv3d.argtypes = [_vp, _vp, _vp, _vp, _vp] + [_c_i] * 8 + [_vp]
 _lib.sg_conv3d_wgrad.argtypes = [_vp, _vp, _vp, _vp] + [_c_i] * 6 + [_vp]
@@ -96,7 +108,7 @@ _lib.sg_pack_target.argtypes = [_vp, _vp, _vp, _c_i, _c_i, _c_i, _c_i, _f32, _f3
 _lib.sg_mse.argtypes = [_vp, _c_i, _vp, _c_i, _vp, _vp, _vp, _c_i, _c_i, _c_dbl, _vp]
 _lib.sg_adam.argtypes = [_vp, _vp, _vp, _vp, _c_i64, _f32, _f32, _f32, _f32, _c_i, _vp, _vp, _c_i, _c_i, _vp]
 for _f in ("mp_init", "mp_init_batch", "mp_step", "mp_vacf", "mp_mass", "mp_info", "mp_get_field",
-           "mp_set_field", "lb_steady", "mp_classify", "mp_step_noalloc", "mp_group_create",
+           "mp_set_field", "lb_steady", "mp_classify", "mp_step_noalloc", "mp_group_create", "mp_grid_wait_selftest",
            "mp_group_step", "mp_group_block_size", "sg_conv3d", "sg_conv3d_wgrad", "sg_pool2",
            "sg_pool2_grad", "sg_up2", "sg_up2_grad", "sg_add", "sg_relu_grad", "sg_pack_input",
            "sg_unpack_output", "sg_pack_target", "sg_mse", "sg_adam"):
@@ -107,6 +119,14 @@ class MPError(RuntimeError):
     def __init__(self, code, msg):
         super().__init__(f"libmp status {code}: {msg}")
         self.code = code
+
+
+class MPBufferError(MPError, ValueError):
+    """A buffer that does not match the C ABI's documented layout, refused by the binding
+    before any library call (status MP_EINVAL; also a ValueError)."""
+
+    def __init__(self, msg):
+        super().__init__(MP_EINVAL, msg)
 
 
 def mp_last_error() -> str:
@@ -136,7 +156,7 @@ def _check_dev_f32(buf, n, name):
     if buf is not None and hasattr(buf, "numel") and hasattr(buf, "dtype"):
         if (not getattr(buf, "is_cuda", False) or str(buf.dtype) != "torch.float32" or not buf.is_contiguous()
                 or buf.numel() < n):
-            raise ValueError(f"{name}: needs a contiguous CUDA float32 tensor of at least {n} values, got "
+            raise MPBufferError(f"{name}: needs a contiguous CUDA float32 tensor of at least {n} values, got "
                              f"shape {tuple(buf.shape)}, {buf.dtype}, on {getattr(buf, 'device', '?')}")
 
 
@@ -144,7 +164,7 @@ def _host_f64(a, n, name):
     """A host numpy float64 array of exactly n values that the library may read or write
     in place (C-contiguous)."""
     if not (isinstance(a, np.ndarray) and a.dtype == np.float64 and a.flags.c_contiguous and a.size == n):
-        raise ValueError(f"{name}: needs a C-contiguous float64 numpy array of {n} values")
+        raise MPBufferError(f"{name}: needs a C-contiguous float64 numpy array of {n} values")
     return a.ctypes.data_as(_dp)
 
 
@@ -178,8 +198,11 @@ def mp_default_options() -> mp_options:
 
 
 def _options(precision="fp32", directions="x", init_density="equilibrium", allow_negative=False,
-             capacity=0, stream=None, rounding="stochastic"):
+             capacity=0, stream=None, rounding="stochastic", scheme="flux", autotune=False, variant=0):
     o = mp_default_options()
+    o.scheme = {"flux": MP_SCHEME_FLUX, "direct": MP_SCHEME_DIRECT}[scheme]
+    o.autotune = int(bool(autotune))
+    o.variant = int(variant)
     o.precision = {"fp32": MP_FP32, "fp64": MP_FP64, "fp16": MP_FP16}[precision]
     o.rounding = {"stochastic": MP_ROUND_STOCHASTIC, "nearest": MP_ROUND_NEAREST}[rounding]
     o.directions = sum({"x": 1, "y": 2, "z": 4}[d] for d in directions)
@@ -213,6 +236,7 @@ class Context:
 def mp_init(solid, u, D_b, k_a, k_d, **options) -> Context:
     """mp_init of include/mp.h. solid: host numpy or device tensor (nz,ny,nx) uint8;
     u: device FP32 buffer of 3*N values (SoA) or None. Options: precision ("fp32"/"fp64"/"fp16"),
+    scheme ("flux"/"direct"), autotune (direct scheme), variant (MP_VARIANT_* flags),
     rounding of fp16 storage ("stochastic"/"nearest"),
     directions (e.g. "x", "xz"), init_density ("equilibrium"/"uniform"), allow_negative,
     capacity, stream."""
@@ -238,6 +262,19 @@ def mp_init_batch(solid, u, D_b, k_a, k_d, **options) -> Context:
 
 def mp_step(ctx: Context, n: int):
     _check(_lib.mp_step(ctx.ptr, int(n)))
+
+
+def mp_variant(ctx: Context) -> str:
+    """How mp_step runs this context ("flux", or the direct scheme's launch form, link terms
+    and block size)."""
+    return _lib.mp_variant(ctx.ptr).decode()
+
+
+def mp_grid_wait_selftest(n_blocks: int, rounds: int, unreachable: bool, timeout_ns: int, stream=None):
+    """mp_grid_wait_selftest of include/mp.h; raises MPError (code MP_ETIMEOUT) when a wait
+    gave up."""
+    _check(_lib.mp_grid_wait_selftest(int(n_blocks), int(rounds), int(bool(unreachable)), int(timeout_ns),
+                                      _stream(stream)))
 
 
 def mp_vacf(ctx: Context, species: int = 0, direction: int = 0, cap: int | None = None):
@@ -301,15 +338,45 @@ def mp_classify(solid, stream=None):
     return cls, (nf.value, ni.value, nc.value)
 
 
+def _device_of(buf):
+    return str(getattr(buf, "device", "?"))
+
+
 def mp_step_noalloc(solid, u, D_b, k_a, k_d, direction, X, X_ads, X_out, X_ads_out, Z_out,
                     stream=None):
     """mp_step_noalloc of include/mp.h: one step of one field on caller-owned device arrays
     (torch CUDA tensors), allocating nothing. solid: uint8 (nz, ny, nx); u: FP32 (3, nz, ny,
-    nx) or None; X, X_ads, X_out, X_ads_out: FP32 (nz, ny, nx); Z_out: one FP64 element."""
+    nx) or None; X, X_ads, X_out, X_ads_out: FP32 (nz, ny, nx); Z_out: one FP64 element.
+    Every tensor is checked against that layout (CUDA, dtype, contiguity, size, one device)
+    before the call, which then runs with that device current."""
+    if not (hasattr(solid, "data_ptr") and getattr(solid, "is_cuda", False) and len(solid.shape) == 3
+            and str(solid.dtype) in ("torch.uint8", "torch.bool") and solid.is_contiguous()):
+        raise MPBufferError(f"solid: needs a contiguous CUDA uint8 tensor (nz, ny, nx), got "
+                            f"{getattr(solid, 'shape', '?')}, {getattr(solid, 'dtype', '?')}")
     nz, ny, nx = solid.shape
-    _check(_lib.mp_step_noalloc(nx, ny, nz, _addr(solid), _addr(u), float(D_b), float(k_a), float(k_d),
-                                int(direction), _addr(X), _addr(X_ads), _addr(X_out), _addr(X_ads_out),
-                                _addr(Z_out), _stream(stream)))
+    N = nx * ny * nz
+    bufs = [("solid", solid)]
+    for name, buf, n in (("u", u, 3 * N), ("X", X, N), ("X_ads", X_ads, N), ("X_out", X_out, N),
+                         ("X_ads_out", X_ads_out, N)):
+        if buf is None and name != "u":
+            raise MPBufferError(f"{name}: a CUDA float32 tensor of {n} values is required")
+        if buf is not None and not hasattr(buf, "numel"):
+            raise MPBufferError(f"{name}: needs a CUDA tensor")
+        _check_dev_f32(buf, n, name)
+        if buf is not None:
+            bufs.append((name, buf))
+    if not (hasattr(Z_out, "numel") and getattr(Z_out, "is_cuda", False) and str(Z_out.dtype) == "torch.float64"
+            and Z_out.numel() >= 1):
+        raise MPBufferError("Z_out: needs a CUDA float64 tensor of at least one element")
+    bufs.append(("Z_out", Z_out))
+    devs = {_device_of(b) for _, b in bufs}
+    if len(devs) != 1:
+        raise MPBufferError(f"all buffers must be on one device, got {sorted(devs)}")
+    import torch
+    with torch.cuda.device(solid.device):
+        _check(_lib.mp_step_noalloc(nx, ny, nz, _addr(solid), _addr(u), float(D_b), float(k_a), float(k_d),
+                                    int(direction), _addr(X), _addr(X_ads), _addr(X_out), _addr(X_ads_out),
+                                    _addr(Z_out), _stream(stream)))
 
 
 class Group:
@@ -345,6 +412,10 @@ def mp_group_step(group: Group, n: int):
 
 def mp_group_block_size(group: Group) -> int:
     return int(_lib.mp_group_block_size(group.ptr))
+
+
+def mp_group_variant(group: Group) -> str:
+    return _lib.mp_group_variant(group.ptr).decode()
 
 
 def mp_group_free(group: Group):

@@ -92,3 +92,27 @@ def test_documented_buffers_pass(mp):
         mp._check_dev_f32(FakeCuda(shape), n, "buf")
     mp._check_dev_f32(None, 10, "buf")
     assert mp._host_f64(np.zeros(7), 7, "Z") is not None
+
+
+def test_noalloc_binding_refuses_mismatched_buffers(mp):
+    solid = FakeCuda((4, 5, 6), dtype=torch.uint8)
+    N = 4 * 5 * 6
+    ok = [FakeCuda((4, 5, 6)) for _ in range(4)]
+    z = FakeCuda((1,), dtype=torch.float64)
+    other = FakeCuda((4, 5, 6))
+    other.device = "cuda:1"
+    cases = [
+        ((FakeCuda((4, 5, 6), dtype=torch.int32), None, *ok, z), "solid"),
+        ((FakeCuda((N,), dtype=torch.uint8), None, *ok, z), "solid"),
+        ((solid, FakeCuda((3 * N - 1,)), *ok, z), "u"),
+        ((solid, None, FakeCuda((4, 5, 6), dtype=torch.float16), *ok[1:], z), "X"),
+        ((solid, None, *ok[:3], FakeCuda((N - 1,)), z), "X_ads_out"),
+        ((solid, None, *ok[:2], FakeCuda((4, 5, 6), contiguous=False), ok[3], z), "X_out"),
+        ((solid, None, *ok, FakeCuda((1,), dtype=torch.float32)), "Z_out"),
+        ((solid, None, *ok[:3], other, z), "one device"),
+        ((solid, None, ok[0], None, *ok[2:], z), "X_ads"),
+    ]
+    for (sd, u, x, xa, xo, xao, zo), what in cases:
+        with pytest.raises(mp.MPError, match=what) as e:
+            mp.mp_step_noalloc(sd, u, 0.05, 0.0, 0.0, 0, x, xa, xo, xao, zo)
+        assert e.value.code == mp.MP_EINVAL and isinstance(e.value, ValueError)
