@@ -151,6 +151,74 @@ def aggregate(seconds, units_per_rank, world, dist=None, device=None):
     return slowest, units_per_rank * world / slowest
 
 
+# Probe of the MP step on a working set far beyond L2 (the scaled probe of the scope table:
+# the benchmark's medium generator at 384^3 with four species), timed inside the default run
+# for the HBM roofline. Inputs are synthetic: the seeded drift flow of media.drift_flow (the
+# step's cost does not depend on the flow's values) and four species with every p_i > 0.
+PROBE = {"lattice": 384, "radius": 6, "porosity": 0.40, "seed": 1, "species": 4, "steps": 200,
+         "flow": "media.drift_flow(mean 0.01, noise 0.01, seed 3)", "species_seed": 7,
+         "D_b": [0.03, 0.1], "k": [1e-3, 1e-1]}
+
+
+def run_hbm_probe(mp, peak, peak_kind, scheme_opts):
+    """Times PROBE["steps"] MP steps of the 384^3 x 4-species probe with CUDA events on the
+    context's stream; returns the roofline entry of its step kernel (algorithmic bytes per
+    step as for the main workload, per node-species)."""
+    import torch
+    from paper_1303_2470_gb300 import media
+    n = PROBE["lattice"]
+    solid, _ = media.random_spheres((n, n, n), PROBE["radius"], PROBE["porosity"], PROBE["seed"])
+    u = torch.as_tensor(media.drift_flow(solid, 0.01, 0.01, seed=3).astype(np.float32)).cuda()
+    Db, ka, kd = media.species(PROBE["species"], seed=PROBE["species_seed"], D_b=tuple(PROBE["D_b"]),
+                               k=tuple(PROBE["k"]))
+    stream = torch.cuda.Stream()
+    steps = PROBE["steps"]
+    ctx = mp.mp_init_batch(torch.as_tensor(solid).cuda(), u, Db, ka, kd, capacity=steps + 60, stream=stream,
+                           **scheme_opts)
+    del u
+    mp.mp_step(ctx, 10)
+    info = mp.mp_info(ctx)
+    variant = mp.mp_variant(ctx)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    e0.record(stream)
+    mp.mp_step(ctx, steps)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    step_s = e0.elapsed_time(e1) / 1e3 / steps
+    S, nf, ni = PROBE["species"], int(info["n_fluid"]), int(info["n_interface"])
+    nbytes = nf * (16 * S + 13) + ni * 16 * S
+    ctx.close()
+    if variant == "flux":
+        name, src = "k_step<float,multi>", "mp.cu"
+    else:
+        name = "k_direct_persistent" if variant.startswith("persistent") else "k_direct_step"
+        src = "mp_direct.cu"
+    tr = TRAFFIC.get(name + "@probe")
+    traffic = tr["bytes_per_launch"] if tr and tr["src_sha"] == _src_sha(src) else None
+    gbs = nbytes / step_s / 1e9
+    return {"kernel": name, "variant": variant, "bound": "hbm", "achieved": gbs, "peak": peak, "unit": "GB/s",
+            "frac": gbs / peak, "traffic": traffic, "algorithmic_bytes_per_step": nbytes,
+            "us_per_step": step_s * 1e6, "node_species_updates_per_s": nf * S / step_s,
+            "workload": f"random spheres {n}^3 (R={PROBE['radius']}, porosity {PROBE['porosity']}, seed "
+                        f"{PROBE['seed']}), {S} species, {PROBE['flow']}; {nf} fluid, {ni} interfacial nodes; "
+                        f"working set > 4x L2",
+            "peak_source": f"{peak_kind} (MEASURED_PEAKS.json hbm_gbs)" if peak_kind == "measured"
+            else "fallback 6.8 TB/s"}
+
+
+def mp_kernel_launches(variant, steps, tuned):
+    """Kernels of mp_step(steps) and of the direct scheme's set-up: the flux scheme launches one
+    kernel per step; the direct scheme one per step plus one that appends the last step's
+    series per run (graphs of 64 steps are runs), or one persistent launch; its set-up adds
+    the table kernel and, when tuned, 20 + 2 steps of each of the six one-step candidates (with
+    their closing launches) and two launches of each of the six persistent ones."""
+    if variant == "flux":
+        return steps
+    run = 1 if variant.startswith("persistent") else steps + -(-steps // 64)
+    return run + 1 + (6 * (22 + 2) + 6 * 2 if tuned else 0)
+
+
 def make_medium():
     from paper_1303_2470_gb300 import media
     nz, ny, nx = WORKLOAD["lattice"][::-1]
@@ -473,6 +541,8 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-probe", action="store_true",
+                    help="skip the 384^3 x 4-species probe of the step beyond L2 (roofline_hbm)")
     ap.add_argument("--mp-steps", type=int, default=WORKLOAD["mp_steps"])
     ap.add_argument("--precision", default="fp32", choices=["fp32", "fp16"],
                     help="field storage of the MP step: fp32 (default) or binary16 with FP32 "
@@ -584,7 +654,8 @@ def main():
         lb_steps_all.append(steps)
         # kernels: the LB and MP steps, one two-iterate mean per failed residual check, and
         # the job's one-off kernels (geometry, cluster labelling, initialisation)
-        launches += steps + max(steps // WORKLOAD["lb_check_every"] - 1, 0) + WORKLOAD["mp_steps"] + JOB_FIXED_LAUNCHES
+        launches += (steps + max(steps // WORKLOAD["lb_check_every"] - 1, 0) + JOB_FIXED_LAUNCHES
+                     + mp_kernel_launches(info["variant"], WORKLOAD["mp_steps"], args.variant < 0))
         ctx.close()
     torch.cuda.synchronize()
     if world > 1:
@@ -653,7 +724,11 @@ def main():
                        force_x=Fx, l2="256 MiB buffer written between timed jobs",
                        parallelism="replicas" if world > 1 else "single GPU"),
         "lb": {"steps_to_steady": lb_steps_all, "ms": lb_ms / args.steps,
-               "mlups": n_fluid * lb_steps_mean / (lb_ms / args.steps / 1e3) / 1e6},
+               "mlups": n_fluid * lb_steps_mean / (lb_ms / args.steps / 1e3) / 1e6,
+               "check_every": WORKLOAD["lb_check_every"], "tol": WORKLOAD["lb_tol"],
+               "iteration": "BGK steps; at every failed residual check the populations are replaced by the "
+                            "mean of the last two iterates (reading R16), so steps_to_steady counts steps "
+                            "of that iteration"},
         "mp": {"ms": mp_ms / args.steps, "init_ms": init_ms / args.steps,
                "kernel_rate": units_per_job / (mp_ms / args.steps / 1e3)},
         "kernels": kern,
@@ -663,6 +738,8 @@ def main():
         "gpu_launches": launches,
         "clocks": clk,
     }
+    if rank == 0 and not args.no_probe:
+        line["roofline_hbm"] = run_hbm_probe(mp, peak, peak_kind, scheme_options(args))
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         line["cpu_baseline"] = oracle_sample(solid, int(round(lb_steps_mean)))
         line["cpu_baseline"].pop("job_s_estimate", None)
