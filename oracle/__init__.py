@@ -244,10 +244,11 @@ def lb_step(solid, f, force, tau=1.0, forced=None):
 
 
 def lb_steady(solid, force, tau=1.0, tol=1e-7, max_steps=200000, check_every=100, u_init=None,
-              rho_init=None, with_rho=False):
+              rho_init=None, with_rho=False, with_f=False):
     """Steady BGK flow, force on the largest fluid cluster, started from f^eq(rho_init, u_init)
     (rest and unit density by default); returns (u[3,nz,ny,nx], steps, residual, converged),
-    plus the final density rho[nz,ny,nx] (0 on solids) when with_rho."""
+    plus the final density rho[nz,ny,nx] (0 on solids) when with_rho, plus the final
+    populations f[19,nz,ny,nx] when with_f."""
     s = np.ascontiguousarray(solid, dtype=np.uint8)
     nz, ny, nx = s.shape
     u = np.zeros((3,) + s.shape)
@@ -255,6 +256,7 @@ def lb_steady(solid, force, tau=1.0, tol=1e-7, max_steps=200000, check_every=100
     F = (ctypes.c_double * 3)(*[float(v) for v in force])
     steps = ctypes.c_int64()
     res = ctypes.c_double()
+    fo = np.zeros((19,) + s.shape) if with_f else None
     ui = None if u_init is None else np.ascontiguousarray(u_init, dtype=np.float64)
     ri = None if rho_init is None else np.ascontiguousarray(rho_init, dtype=np.float64)
     rc = _load().or_lb_steady(nx, ny, nz, _ptr(s, _u8p), F, ctypes.c_double(tau),
@@ -262,8 +264,10 @@ def lb_steady(solid, force, tau=1.0, tol=1e-7, max_steps=200000, check_every=100
                               ctypes.c_int64(check_every),
                               _ptr(ui, _dp) if ui is not None else _dp(),
                               _ptr(ri, _dp) if ri is not None else _dp(), _ptr(u, _dp), _ptr(rho, _dp),
-                              ctypes.byref(steps), ctypes.byref(res))
+                              ctypes.byref(steps), ctypes.byref(res), _ptr(fo, _dp) if with_f else _dp())
     if rc < 0:
         raise ValueError("oracle LB rejected its input")
     out = (u, steps.value, res.value, rc == 0)
-    return out + (rho,) if with_rho else out
+    if with_rho:
+        out = out + (rho,)
+    return out + (fo,) if with_f else out

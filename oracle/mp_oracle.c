@@ -625,7 +625,7 @@ int or_lb_step(int nx, int ny, int nz, const uint8_t* solid, const uint8_t* forc
 int or_lb_steady(int nx, int ny, int nz, const uint8_t* solid, const double F[3], double tau,
                  double tol, int64_t max_steps, int64_t check_every, const double* u_init,
                  const double* rho_init, double* u_out, double* rho_out, int64_t* steps_out,
-                 double* residual_out)
+                 double* residual_out, double* f_out)
 {
     int64_t N = (int64_t)nx * ny * nz;
     if (tau <= 0.5 || max_steps < 1 || check_every < 1) return -1;
@@ -682,6 +682,7 @@ int or_lb_steady(int nx, int ny, int nz, const uint8_t* solid, const double F[3]
         }
     if (steps_out) *steps_out = t;
     if (residual_out) *residual_out = res;
+    if (f_out) memcpy(f_out, f, sizeof(double) * NQ * N); /* the final populations */
     free(f); free(fn); free(u); free(uprev); free(forced);
     return rc;
 }
