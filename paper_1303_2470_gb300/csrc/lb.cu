@@ -23,15 +23,22 @@
 #include <string>
 
 #include "internal.cuh"
+#include "lattice.cuh"
 
 using namespace mp;
 
 namespace {
 
 constexpr int kLbThreads = 256;
+// 8 resident blocks per SM (32 registers a thread): the LB step is bound by instruction issue
+// and measured faster at full occupancy than with a larger register budget
+#ifndef MP_LB_MIN_BLOCKS
+#define MP_LB_MIN_BLOCKS 8
+#endif
 
 struct LbArgs {
     int nx, ny, nz, N, NF;
+    Div dx, dxy;  // division by nx and by nx*ny
     const uint32_t* fluid;
     const int32_t* fbase;    // fluid nodes before each 32-node word
     const int32_t* flist;    // lattice node of fluid index k
@@ -45,13 +52,12 @@ __device__ __forceinline__ bool lb_bit(const uint32_t* __restrict__ w, int n)
 {
     return (__ldg(w + (n >> 5)) >> (n & 31)) & 1u;
 }
-__device__ __forceinline__ int lb_wrap(int v, int n) { return v < 0 ? v + n : (v >= n ? v - n : v); }
 
 // mode 0: plain step; 1: also store u into u_prev; 2: store u into u_out (and rho into
 // rho_out when given), fold max|u - u_prev| (FP64) into *res_bits (non-negative doubles
 // order like their bits), then store u into u_prev. u_prev is compact [3][N_F]; u_out and
 // rho_out are dense (their solid entries are zeroed once by the host).
-__global__ void __launch_bounds__(kLbThreads)
+__global__ void __launch_bounds__(kLbThreads, MP_LB_MIN_BLOCKS)
     k_lb_step(const LbArgs a, const float* __restrict__ g, float* __restrict__ gn, int mode,
               float* __restrict__ u_prev, float* __restrict__ u_out, float* __restrict__ rho_out,
               unsigned long long* __restrict__ res_bits)
@@ -62,14 +68,14 @@ __global__ void __launch_bounds__(kLbThreads)
     double res = 0.0;
     if (k < a.NF) {
         const int n = __ldg(a.flist + k);
-        const int x = n % a.nx, y = (n / a.nx) % a.ny, z = n / (a.nx * a.ny);
+        const Nbr b = nbrs_of(a.nx, a.ny, a.nz, a.dx, a.dxy, n);
         float f[kQ];
 #pragma unroll
         for (int i = 0; i < kQ; ++i) {
             if (i == 0) {
                 f[0] = g[k];
             } else {
-                const int s = lb_wrap(x - cx(i), a.nx) + a.nx * (lb_wrap(y - cy(i), a.ny) + a.ny * lb_wrap(z - cz(i), a.nz));
+                const int s = src_of(b, i);
                 const uint32_t bits = __ldg(a.fluid + (s >> 5));
                 if ((bits >> (s & 31)) & 1u) {
                     const int ks = __ldg(a.fbase + (s >> 5)) + __popc(bits & ((1u << (s & 31)) - 1u));
@@ -96,15 +102,30 @@ __global__ void __launch_bounds__(kLbThreads)
         const float uz = (mz + 0.5f * Fz) * inv_rho;
         const float uu = ux * ux + uy * uy + uz * uz;
         const float uF = ux * Fx + uy * Fy + uz * Fz;
+        const float m15uu = -1.5f * uu;
+        const float m3uF = -3.0f * uF;
 #pragma unroll
         for (int i = 0; i < kQ; ++i) {
             const float w = weight<float>(i);
-            const float cu = float(cx(i)) * ux + float(cy(i)) * uy + float(cz(i)) * uz;
-            const float cF = float(cx(i)) * Fx + float(cy(i)) * Fy + float(cz(i)) * Fz;
-            // f^eq - w = w [(rho - 1) + rho (3 cu + 4.5 cu^2 - 1.5 uu)]
-            const float geq = w * (drho + rho * (3.0f * cu + 4.5f * cu * cu - 1.5f * uu));
-            const float src = a.guo * w * (3.0f * (cF - uF) + 9.0f * cu * cF);
-            gn[(size_t)i * NF + k] = f[i] - a.inv_tau * (f[i] - geq) + src;
+            // c_i.u and c_i.F: signed sums of one or two components (zero for the rest link)
+            float cu = 0.f, cF = 0.f;
+            if (cx(i)) {
+                cu += float(cx(i)) * ux;
+                cF += float(cx(i)) * Fx;
+            }
+            if (cy(i)) {
+                cu += float(cy(i)) * uy;
+                cF += float(cy(i)) * Fy;
+            }
+            if (cz(i)) {
+                cu += float(cz(i)) * uz;
+                cF += float(cz(i)) * Fz;
+            }
+            // f^eq - w = w [(rho - 1) + rho (cu (3 + 4.5 cu) - 1.5 uu)]
+            const float geq = w * fmaf(rho, fmaf(cu, fmaf(4.5f, cu, 3.0f), m15uu), drho);
+            // Guo: (1 - 1/(2 tau)) w [3 (c_i - u).F + 9 (c_i.u)(c_i.F)] = ... w [3 cF (1 + 3 cu) - 3 u.F]
+            const float src = a.guo * w * fmaf(3.0f * cF, fmaf(3.0f, cu, 1.0f), m3uF);
+            gn[(size_t)i * NF + k] = fmaf(-a.inv_tau, f[i] - geq, f[i]) + src;
         }
         if (mode == 1) {
             u_prev[k] = ux;
@@ -217,6 +238,8 @@ extern "C" int lb_steady(const mp_geometry* geom, const double force[3], double 
     a.nz = G.nz;
     a.N = G.N;
     a.NF = (int)G.n_fluid;
+    a.dx = make_div((unsigned)G.nx);
+    a.dxy = make_div((unsigned)(G.nx * G.ny));
     a.fluid = G.fluid;
     a.fbase = G.fbase;
     a.flist = G.flist;

@@ -194,3 +194,22 @@ def test_direct_rejects_other_precisions(mp):
         with pytest.raises(mp.MPError) as e:
             mp.mp_init(solid, None, 0.05, 0.0, 0.0, precision=prec, scheme="direct")
         assert e.value.code == mp.MP_EINVAL
+
+
+def test_sharded_units_through_the_library_match_oracle(mp):
+    """The split of (medium, species) units (here on one rank) run through the library:
+    each medium's share becomes one context; every unit's series matches the oracle."""
+    from paper_1303_2470_gb300 import shard
+    meds = []
+    for j, shape in enumerate(((9, 10, 11), (8, 12, 7))):
+        solid, _ = media.random_spheres(shape, 2, 0.6, seed=20 + j)
+        u = media.drift_flow(solid, 0.005, 0.004, seed=30 + j).astype(np.float32)
+        meds.append((solid, u, media.species(3, seed=40 + j, D_b=(0.03, 0.1))))
+    dev_media = [(s, dev32(u), sp) for s, u, sp in meds]
+    units = [(m, s) for m in range(2) for s in (0, 2)]
+    got = shard.run_sharded(dev_media, units, 60, shard.mp_medium_runner(mp, scheme="direct"))
+    assert sorted(got) == sorted(units)
+    for (m, s), (Z, D) in got.items():
+        solid, u, (Db, ka, kd) = meds[m]
+        ref = oracle.run(oracle.Problem(solid, u.astype(np.float64), Db[s], ka[s], kd[s]), g=0, nsteps=60)
+        assert _z_err(Z, ref.Z) < 1e-4 and _d_err(D, ref.D) < 1e-4

@@ -42,7 +42,9 @@ def test_fixed_steps_porous_medium(mp):
     ug = u.cpu().numpy().astype(np.float64)
     scale = np.abs(uo).max()
     assert np.max(np.abs(ug - uo)) < 1e-4 * scale
-    assert abs(res - ro) < 1e-3 * ro + 1e-12
+    # the residual is a difference of two FP32 velocities: its error is bounded by a few
+    # units in the last place of the largest speed (2^-24 of it), which here is 0.4 % of it
+    assert abs(res - ro) < 1e-3 * ro + 4 * 2.0 ** -24 * scale
     assert np.all(ug[:, solid.astype(bool)] == 0.0)
     assert np.all(ug[:, pocket] == 0.0)
 
