@@ -68,6 +68,14 @@ TRAFFIC = {
     # mp.cu 'cd4af1701d41b82f'; the file changed since only in the flow-packing kernel (64-bit
     # offsets), not in k_step.
     "k_step<float>": {"bytes_per_launch": 48_607_488 + 1_392_640, "src_sha": "450a088ead29ab87"},
+    # ncu --set full, python bench.py --profile --scheme direct --variant 2: one persistent
+    # launch of 20 steps moved 1292.18 + 93.32 MB; per step (the unit of the roofline entry)
+    "k_direct_persistent": {"bytes_per_launch": (1_292_180_000 + 93_321_472) // 20, "src_sha": "84dbbcb7b51b3436"},
+    # ncu --set full, python bench.py --profile-probe --scheme direct --variant 1: one step of
+    # 192^3 x 4 species (2 830 813 fluid nodes) moved 369.79 + 135.12 MB; scaled by the units to
+    # the 384^3 x 4 probe (22 649 211 fluid nodes)
+    "k_direct_step@probe": {"bytes_per_launch": int((369_790_464 + 135_121_408) * 22_649_211 / 2_830_813),
+                            "src_sha": "84dbbcb7b51b3436"},
 }
 
 
@@ -465,6 +473,29 @@ def run_surrogate(args):
     return 0
 
 
+def run_profile_probe(args):
+    """A smaller case of the beyond-L2 probe for ncu --set full captures (python bench.py
+    --profile-probe): 192^3 random spheres (R = 6, porosity 0.40, seed 1) x 4 species, about
+    1 GB on the device, 20 MP steps with the scheme and variant given."""
+    import torch
+    from paper_1303_2470_gb300 import build, media
+    build.build()
+    from paper_1303_2470_gb300 import mp
+    n = 192
+    solid, _ = media.random_spheres((n, n, n), PROBE["radius"], PROBE["porosity"], PROBE["seed"])
+    u = torch.as_tensor(media.drift_flow(solid, 0.01, 0.01, seed=3).astype(np.float32)).cuda()
+    Db, ka, kd = media.species(PROBE["species"], seed=PROBE["species_seed"], D_b=tuple(PROBE["D_b"]),
+                               k=tuple(PROBE["k"]))
+    ctx = mp.mp_init_batch(torch.as_tensor(solid).cuda(), u, Db, ka, kd, capacity=64, **scheme_options(args))
+    mp.mp_step(ctx, 20)
+    torch.cuda.synchronize()
+    info = mp.mp_info(ctx)
+    print(json.dumps({"profile_probe": "ok", "n_fluid": info["n_fluid"], "n_interface": info["n_interface"],
+                      "variant": mp.mp_variant(ctx)}))
+    ctx.close()
+    return 0
+
+
 def run_profile_batched():
     """Two random-sphere media (96^3, 128^3) x 16 species, 30 LB steps each, then 8 grouped
     steps without graph or autotune: `k_step_group` launches for ncu captures."""
@@ -553,6 +584,8 @@ def main():
                          "steps to steady from the learned warm start vs the cold start")
     ap.add_argument("--profile-batched", action="store_true",
                     help="short grouped run (96^3 and 128^3 media x 16 species) for ncu captures")
+    ap.add_argument("--profile-probe", action="store_true",
+                    help="20 MP steps of a 192^3 x 4-species case of the beyond-L2 probe for ncu captures")
     ap.add_argument("--profile-surrogate", action="store_true",
                     help="two forward passes of the warm-start network on a 128^3 box for ncu captures")
     ap.add_argument("--scheme", default="direct", choices=["direct", "flux"],
@@ -572,6 +605,8 @@ def main():
         return run_profile_case(args)
     if args.profile_batched:
         return run_profile_batched()
+    if args.profile_probe:
+        return run_profile_probe(args)
     if args.profile_surrogate:
         return run_profile_surrogate()
     if args.workload == "batched":
