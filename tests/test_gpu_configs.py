@@ -53,6 +53,7 @@ def _check(Z, D, ref, what):
     assert Z.size > t[-1], what
     z_err = np.max(np.abs(Z[t] - Zo)) / abs(Zo[0])
     d_err = np.max(np.abs(D[t] - Do) / np.abs(Do))
+    print(f"{what}: Z/Z(0) error {z_err:.3e}, D relative error {d_err:.3e}")
     assert z_err < 1e-4, f"{what}: Z/Z(0) error {z_err:.3e}"
     assert d_err < 1e-4, f"{what}: D relative error {d_err:.3e}"
     return z_err, d_err
