@@ -312,9 +312,12 @@ BATCHED = {
 
 def run_batched(args):
     """Config of batched species and uneven media: every medium gets its LB flow, then all
-    48 species advance (a) in one grouped launch per step (CUDA graph, autotuned block) and
-    (b) one species per launch; both are timed over the same number of steps. The fields
-    of (a) and (b) are identical (tests/test_gpu_group.py), so the accuracy is equal."""
+    48 species advance (a) as one group of the three contexts, for each scheme (direct: the
+    autotuned variant, one launch per step or one persistent launch; flux: one launch per
+    step, CUDA graph, autotuned block), and (b) one species per launch (flux); all timed over
+    the same number of steps. Grouped and one-species fields are identical for a scheme
+    (tests/test_gpu_group.py, tests/test_gpu_direct.py), and both schemes meet the oracle bar
+    on these media (tests/test_gpu_configs.py)."""
     import torch
     from paper_1303_2470_gb300 import build, media
     build.build()
@@ -345,15 +348,19 @@ def run_batched(args):
         torch.cuda.synchronize()
         return e0.elapsed_time(e1) / 1e3
 
-    ctxs = [mp.mp_init_batch(sd, u, Db, ka, kd, capacity=cap, allow_negative=True)
-            for sd, u, Db, ka, kd, *_ in meds]
-    g = mp.mp_group_create(ctxs, graph_steps=64, autotune=True)
-    mp.mp_group_step(g, 10)
-    t_group = timed(lambda: mp.mp_group_step(g, steps))
-    block = mp.mp_group_block_size(g)
-    g.close()
-    for c in ctxs:
-        c.close()
+    grouped = {}
+    for scheme in ("direct", "flux"):
+        ctxs = [mp.mp_init_batch(sd, u, Db, ka, kd, capacity=cap, allow_negative=True, scheme=scheme)
+                for sd, u, Db, ka, kd, *_ in meds]
+        g = mp.mp_group_create(ctxs, graph_steps=64, autotune=True)
+        mp.mp_group_step(g, 10)
+        t = timed(lambda: mp.mp_group_step(g, steps))
+        grouped[scheme] = {"updates_per_s": units / t, "ms_per_step": t / steps * 1e3,
+                           "variant": mp.mp_group_variant(g), "block": mp.mp_group_block_size(g)}
+        g.close()
+        for c in ctxs:
+            c.close()
+    t_group = units / grouped["direct"]["updates_per_s"]
     singles = [mp.mp_init(sd, u, Db[s], ka[s], kd[s], capacity=cap, allow_negative=True)
                for sd, u, Db, ka, kd, *_ in meds for s in range(BATCHED["species"])]
     for c in singles:
@@ -367,8 +374,9 @@ def run_batched(args):
     for c in singles:
         c.close()
     line = {"metric": "batched sorption-MP node-species updates/s", "workload": BATCHED["workload"],
-            "steps": steps, "grouped": units / t_group, "one_species_per_launch": units / t_single,
-            "speedup": t_single / t_group, "block": block, "graph_steps": 64,
+            "steps": steps, "grouped": units / t_group, "grouped_by_scheme": grouped,
+            "one_species_per_launch": units / t_single, "one_species_per_launch_scheme": "flux",
+            "speedup": t_single / t_group, "graph_steps": 64,
             "media": [{"n": int(m[0].shape[0]), "porosity": m[6], "n_fluid": m[5], "lb_steps": m[7]} for m in meds],
             "unit": UNIT}
     print(json.dumps(line))
