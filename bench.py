@@ -528,7 +528,7 @@ def run_profile_batched():
 
 
 def run_profile_surrogate():
-    """Two forward passes of the trained warm-start network on a 128^3 box (15 `k_conv`
+    """Two forward passes of the trained warm-start network on a 128^3 box (15 `k_conv_tc`
     launches each, in layer order e0a .. out), no timing: for ncu captures of the tensor-core
     convolution (the second pass's d0a, 64 -> 32 channels at full resolution, is launch 27)."""
     import torch

@@ -34,10 +34,19 @@ extern "C" {
  *           gradient with respect to the input (with w in [27][Cin][Cout] order, N = Cin,
  *           K = Cout).
  *  relu     nonzero: act = max(0, .), else identity.
- * Needs K and N multiples of 16, D, H, W >= 1.
+ * Needs K and N multiples of 16, D, H, W >= 1. Runs on the 5th-generation tensor cores
+ * (tcgen05.mma, FP32 accumulators in tensor memory): blocks of 128 voxels x up to 256 output
+ * channels. Its waits are bounded; sg_check reports one that gave up.
  */
 int sg_conv3d(const void* x, const void* w, const float* bias, void* y, float* yf, int B, int D, int H,
               int W, int K, int N, int sign, int relu, void* stream);
+
+/*
+ * sg_check -- synchronises the stream and returns MP_ETIMEOUT (clearing the record) when a
+ * bounded wait inside a tensor-core convolution launched since the last check gave up, so
+ * that its output is not valid; MP_OK otherwise. (No counterpart in the paper.)
+ */
+int sg_check(void* stream);
 
 /*
  * sg_conv3d_wgrad -- dw[tap][ci][co] += sum_{b, v} x[b][v + o_tap][ci] dy[b][v][co] and, when

@@ -1,7 +1,8 @@
 // surrogate.cu -- kernels of the learned warm start for lb_steady (include/surrogate.h): 3x3x3
-// periodic convolutions as implicit GEMMs on the tensor cores (mma.sync m16n8k16, BF16
-// operands, FP32 accumulation), their input and weight gradients, pooling, upsampling,
-// the masked loss and the Adam update. Nothing here belongs to the moment-propagation
+// periodic convolutions as implicit GEMMs on the tensor cores (forward and input-gradient
+// convolutions on the 5th-generation tensor cores, tcgen05.mma with accumulators in tensor
+// memory; the weight gradient with mma.sync m16n8k16; BF16 operands, FP32 accumulation),
+// pooling, upsampling, the masked loss and the Adam update. Nothing here belongs to the moment-propagation
 // method itself; the network's output only seeds lb_steady.
 #include <cuda_bf16.h>
 
@@ -37,163 +38,235 @@ struct ConvArgs {
     int D, H, W, V, K, N, sign, relu;
 };
 
-// four 8x8 BF16 matrices from shared memory (lanes 8j..8j+7 give the row addresses of
-// matrix j): each lane receives (M[l/4][2(l%4)], M[l/4][2(l%4)+1]) of every matrix, which is
-// the m16n8k16 fragment layout of A (row-major) and of B stored as [n][k]
-__device__ __forceinline__ void ldsm_x4(uint32_t& r0, uint32_t& r1, uint32_t& r2, uint32_t& r3, const bf16* p)
+// ---------------------------------------------------------------------------------------
+// Forward (and transposed) convolution on the 5th-generation tensor cores: an implicit GEMM
+// with M = 128 voxels per block, N = the block's output channels (up to 256, one MMA wide),
+// K = 27 taps x K input channels in stages of one tap x up to 64 channels (four MMAs of
+// K = 16). Operands sit in shared memory in the canonical K-major layout without swizzle:
+// 8-row x 16-byte core matrices, the eight k-chunks of a stage of one 8-row group
+// contiguous (1024 bytes), so a descriptor with leading offset 128 (next core matrix along
+// k) and stride offset 1024 (next 8-row group) describes any 16-wide k-slice. The
+// accumulators (FP32) live in tensor memory; one thread issues the MMAs. A ring of three
+// shared-memory stages is filled by asynchronous copies (cp.async, zero-filled outside the
+// volume); the MMAs of a stage signal an mbarrier when they complete, which frees its
+// buffer for the copies of a later stage. The epilogue reads the accumulators back with
+// tcgen05.ld (warp w holds rows 32w..32w+31), adds the bias, applies the ReLU and stores.
+// Every wait is bounded; a wait that gives up records it in g_sg_tc_fail (read by
+// sg_check), and the block still releases its tensor memory.
+// ---------------------------------------------------------------------------------------
+constexpr int kTM = 128;         // voxels per block (MMA M)
+#ifndef SG_TC_KC
+#define SG_TC_KC 32
+#endif
+constexpr int kTKC = SG_TC_KC;   // input channels per stage
+#ifndef SG_TC_STAGES
+#define SG_TC_STAGES 2
+#endif
+constexpr int kTStages = SG_TC_STAGES;  // shared-memory ring
+constexpr int kTThreads = 128;   // four warps: one accumulator row per thread
+constexpr int kTMaxN = 256;      // output channels per block (MMA N)
+constexpr int kTGroup = (kTKC / 8) * 128;  // bytes of one 8-row group of a stage
+constexpr int kTABytes = (kTM / 8) * kTGroup;
+constexpr long long kTWaitNs = 1000000000LL;  // a wait gives up after 1 s of the global timer
+
+__device__ int g_sg_tc_fail;
+
+__device__ __forceinline__ uint32_t smem_u32(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
+
+// shared-memory matrix descriptor: start address, leading byte offset 128 (along k), stride
+// byte offset 1024 (8-row groups), no swizzle, descriptor version 1 (bit 46)
+__device__ __forceinline__ uint64_t tc_desc(uint32_t addr)
 {
-    const uint32_t addr = (uint32_t)__cvta_generic_to_shared(p);
-    asm volatile("ldmatrix.sync.aligned.m8n8.x4.shared.b16 {%0,%1,%2,%3}, [%4];"
-                 : "=r"(r0), "=r"(r1), "=r"(r2), "=r"(r3)
-                 : "r"(addr)
-                 : "memory");
+    return (uint64_t)((addr & 0x3FFFFu) >> 4) | ((uint64_t)(128 >> 4) << 16) | ((uint64_t)(kTGroup >> 4) << 32) |
+           (1ull << 46);
 }
 
-// Forward (and transposed) convolution tile: BM = 128 MT voxels x BN = 8 NT output channels
-// per block of 8 warps (warp w: voxels 16 MT w .. 16 MT (w + 1) - 1, all NT column tiles),
-// reduction over the 27 taps and the input channels in stages of 32 (two m16n8k16 steps).
-// Two shapes: 128 x 64 (MT = 1, NT = 8) for N > 32 and 256 x 32 (MT = 2, NT = 4) for
-// N <= 32, so that the full-resolution 32-channel layers fill their tiles and each B
-// fragment feeds two products. The next stage's operands are loaded into registers while the
-// current one is multiplied, then stored to the other shared buffer: one barrier per stage.
-// Shared rows hold 40 BF16 (80 bytes), so the eight 16-byte rows of an ldmatrix phase, and
-// the staging stores of eight consecutive rows, fall on distinct banks.
-constexpr int kCS = 32, kCLd = 40, kCThreads = 256;
-
-template <int MT, int NT>
-__device__ __forceinline__ void conv_stage_mma(const bf16 (*As)[kCLd], const bf16 (*Bs)[kCLd],
-                                               float (&acc)[MT][NT][4], int ncols)
+// instruction descriptor of kind::f16: FP32 accumulator, BF16 A and B, both K-major,
+// N >> 3 at bit 17, M >> 4 at bit 24
+__host__ __device__ constexpr uint32_t tc_idesc(int n)
 {
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    const int m0 = warp * 16 * MT;
-    // A: matrices (rows 0-7, k 0-7), (rows 8-15, k 0-7), (rows 0-7, k 8-15), (rows 8-15, k 8-15)
-    const int ar = (lane & 7) + ((lane >> 3) & 1) * 8, ac = (lane >> 4) * 8;
-    // B ([n][k]): matrices (tile nt, k 0-7), (nt, k 8-15), (nt + 1, k 0-7), (nt + 1, k 8-15)
-    const int br = (lane & 7) + (lane >> 4) * 8, bc = ((lane >> 3) & 1) * 8;
-#pragma unroll
-    for (int kk = 0; kk < kCS; kk += 16) {
-        uint32_t af[MT][4];
-#pragma unroll
-        for (int mt = 0; mt < MT; ++mt)
-            ldsm_x4(af[mt][0], af[mt][1], af[mt][2], af[mt][3], &As[m0 + mt * 16 + ar][kk + ac]);
-#pragma unroll
-        for (int nt = 0; nt < NT; nt += 2) {
-            if (nt * 8 < ncols) {  // ncols is a multiple of 16: both tiles of the pair or neither
-                uint32_t b0, b1, b2, b3;
-                ldsm_x4(b0, b1, b2, b3, &Bs[nt * 8 + br][kk + bc]);
-#pragma unroll
-                for (int mt = 0; mt < MT; ++mt) {
-                    mma16816(acc[mt][nt], af[mt][0], af[mt][1], af[mt][2], af[mt][3], b0, b1);
-                    mma16816(acc[mt][nt + 1], af[mt][0], af[mt][1], af[mt][2], af[mt][3], b2, b3);
-                }
-            }
-        }
+    return (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(n >> 3) << 17) | ((uint32_t)(kTM >> 4) << 24);
+}
+
+#ifndef SG_TC_CACHE_L1
+#define SG_TC_CACHE_L1 1
+#endif
+// 16-byte asynchronous copy global -> shared (zero-filled beyond `bytes`); through L1, where
+// the tap-shifted tiles of one block overlap
+__device__ __forceinline__ void cp_async16(uint32_t dst, const void* src, uint32_t bytes)
+{
+#if SG_TC_CACHE_L1
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 16, %2;" ::"r"(dst), "l"(src), "r"(bytes) : "memory");
+#else
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;" ::"r"(dst), "l"(src), "r"(bytes) : "memory");
+#endif
+}
+
+__device__ __forceinline__ unsigned long long tc_now_ns()
+{
+    unsigned long long t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
+
+// wait for the phase of parity `parity` of an mbarrier to complete; false after kTWaitNs
+__device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity)
+{
+    const unsigned long long t0 = tc_now_ns();
+    while (true) {
+        uint32_t done;
+        asm volatile(
+            "{\n.reg .pred q;\nmbarrier.try_wait.parity.shared::cta.b64 q, [%1], %2;\nselp.b32 %0, 1, 0, q;\n}"
+            : "=r"(done)
+            : "r"(bar), "r"(parity)
+            : "memory");
+        if (done) return true;
+        if ((long long)(tc_now_ns() - t0) > kTWaitNs) return false;
     }
 }
 
-template <int MT, int NT>
-__global__ void __launch_bounds__(kCThreads) k_conv(const ConvArgs a)
+__global__ void __launch_bounds__(kTThreads) k_conv_tc(const ConvArgs a)
 {
-    constexpr int BM = 128 * MT, BN = 8 * NT;
-    constexpr int AP = 2 * BM / kCThreads;  // A pieces (16 channels of one voxel) per thread
-    static_assert(AP * kCThreads == 2 * BM && BN * 4 <= kCThreads, "staging shape");
-    __shared__ __align__(16) bf16 As[2][BM][kCLd];
-    __shared__ __align__(16) bf16 Bs[2][BN][kCLd];
-    const int tid = threadIdx.x;
-    const int v0 = blockIdx.x * BM, n0 = blockIdx.y * BN, b = blockIdx.z;
-    // A piece p = tid + 256 i: voxel row p % BM, channels 16 (p / BM) .. +15 of the stage;
-    // B: column row tid % BN, channels 8 (tid / BN) .. +7 (threads below 4 BN)
-    int ar[AP], ah[AP], xa[AP], ya[AP], za[AP];
-    bool vok[AP];
-#pragma unroll
-    for (int i = 0; i < AP; ++i) {
-        const int p = tid + kCThreads * i;
-        ar[i] = p % BM;
-        ah[i] = (p / BM) * 16;
-        const int va = v0 + ar[i];
-        vok[i] = va < a.V;
-        xa[i] = ya[i] = za[i] = 0;
-        if (vok[i]) {
-            xa[i] = va % a.W;
-            ya[i] = (va / a.W) % a.H;
-            za[i] = va / (a.W * a.H);
-        }
+    extern __shared__ __align__(1024) unsigned char tc_smem[];
+    __shared__ __align__(8) uint64_t mbar[kTStages];
+    __shared__ uint32_t tmem_base;
+    const int tid = threadIdx.x, warp = tid >> 5;
+    const int n0 = blockIdx.y * kTMaxN;
+    const int BN = a.N - n0 < kTMaxN ? a.N - n0 : kTMaxN;  // a multiple of 16
+    const int BBytes = (BN / 8) * kTGroup;
+    unsigned char* sA = tc_smem;
+    unsigned char* sB = tc_smem + kTStages * kTABytes;
+    const int b = blockIdx.z;
+    const int v = blockIdx.x * kTM + tid;  // this thread's voxel row of A and of the result
+    const bool vok = v < a.V;
+    int xa = 0, ya = 0, za = 0;
+    if (vok) {
+        xa = v % a.W;
+        ya = (v / a.W) % a.H;
+        za = v / (a.W * a.H);
     }
-    const bool bthr = tid < BN * 4;
-    const int br = tid % BN, bq = (tid / BN) * 8;
-    const bool nok = bthr && n0 + br < a.N;
-    const bf16* xb = a.x + (size_t)b * a.V * a.K;
-    const int ncols = a.N - n0 < BN ? a.N - n0 : BN;
-    const int cstages = (a.K + kCS - 1) / kCS;  // channel stages per tap (K is a multiple of 16)
-    const int nst = 27 * cstages;
-    uint4 ra[AP][2], rb;
-    // global -> registers for stage st (zero outside the box of channels, voxels, columns)
-    auto fetch = [&](int st) {
-        const int tap = st / cstages, c0 = (st - tap * cstages) * kCS;
-        const int dz = tap / 9 - 1, dy = (tap / 3) % 3 - 1, dx = tap % 3 - 1;
-#pragma unroll
-        for (int i = 0; i < AP; ++i) {
-            ra[i][0] = ra[i][1] = make_uint4(0u, 0u, 0u, 0u);
-            if (vok[i] && c0 + ah[i] < a.K) {
-                const int xs = wrap(xa[i] + a.sign * dx, a.W), ys = wrap(ya[i] + a.sign * dy, a.H);
-                const int zs = wrap(za[i] + a.sign * dz, a.D);
-                const bf16* p = xb + ((size_t)(zs * a.H + ys) * a.W + xs) * a.K + c0 + ah[i];
-                ra[i][0] = *reinterpret_cast<const uint4*>(p);
-                ra[i][1] = *reinterpret_cast<const uint4*>(p + 8);
-            }
-        }
-        rb = make_uint4(0u, 0u, 0u, 0u);
-        if (nok && c0 + bq < a.K) rb = *reinterpret_cast<const uint4*>(a.w + ((size_t)tap * a.N + n0 + br) * a.K + c0 + bq);
-    };
-    auto stash = [&](int buf) {
-#pragma unroll
-        for (int i = 0; i < AP; ++i) {
-            *reinterpret_cast<uint4*>(&As[buf][ar[i]][ah[i]]) = ra[i][0];
-            *reinterpret_cast<uint4*>(&As[buf][ar[i]][ah[i] + 8]) = ra[i][1];
-        }
-        if (bthr) *reinterpret_cast<uint4*>(&Bs[buf][br][bq]) = rb;
-    };
-    float acc[MT][NT][4];
-#pragma unroll
-    for (int mt = 0; mt < MT; ++mt)
-#pragma unroll
-        for (int i = 0; i < NT; ++i) acc[mt][i][0] = acc[mt][i][1] = acc[mt][i][2] = acc[mt][i][3] = 0.0f;
-    fetch(0);
-    stash(0);
+    const int cst = (a.K + kTKC - 1) / kTKC;  // stages per tap
+    const int nst = 27 * cst;
+    uint32_t ncols = 32;
+    while ((int)ncols < BN) ncols <<= 1;
+    if (tid == 0) {
+        for (int s = 0; s < kTStages; ++s) asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(&mbar[s])));
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    if (warp == 0) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(&tmem_base)),
+                     "r"(ncols));
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
+    }
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
     __syncthreads();
-    for (int st = 0; st < nst; ++st) {
-        const int cur = st & 1;
-        if (st + 1 < nst) fetch(st + 1);
-        conv_stage_mma<MT, NT>(As[cur], Bs[cur], acc, ncols);
-        if (st + 1 < nst) stash(cur ^ 1);
-        __syncthreads();
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+    const uint32_t tmem = tmem_base;
+    const bf16* xb = a.x + (size_t)b * a.V * a.K;
+
+    // asynchronous copies of stage st into ring buffer buf: this thread's A row, and B rows
+    // tid, tid + 128, ... of the block's output channels
+    auto load_stage = [&](int st, int buf) {
+        const int tap = st / cst, c0 = (st - tap * cst) * kTKC;
+        const int kc = a.K - c0 < kTKC ? a.K - c0 : kTKC;
+        const int dz = tap / 9 - 1, dy = (tap / 3) % 3 - 1, dx = tap % 3 - 1;
+        const bf16* src = xb;  // any valid address when the row lies outside the volume
+        if (vok) {
+            const int xs = wrap(xa + a.sign * dx, a.W), ys = wrap(ya + a.sign * dy, a.H), zs = wrap(za + a.sign * dz, a.D);
+            src = xb + ((size_t)(zs * a.H + ys) * a.W + xs) * a.K + c0;
+        }
+        const uint32_t da = smem_u32(sA + buf * kTABytes + (tid >> 3) * kTGroup + (tid & 7) * 16);
+        for (int j = 0; j < kc / 8; ++j) cp_async16(da + j * 128, src + (vok ? 8 * j : 0), vok ? 16u : 0u);
+        for (int n = tid; n < BN; n += kTThreads) {
+            const bf16* ws = a.w + ((size_t)tap * a.N + n0 + n) * a.K + c0;
+            const uint32_t db = smem_u32(sB + buf * BBytes + (n >> 3) * kTGroup + (n & 7) * 16);
+            for (int j = 0; j < kc / 8; ++j) cp_async16(db + j * 128, ws + 8 * j, 16u);
+        }
+    };
+
+    bool ok = true;
+    for (int s = 0; s < kTStages - 1; ++s) {
+        if (s < nst) load_stage(s, s);
+        asm volatile("cp.async.commit_group;" ::: "memory");
     }
-    const int lane = tid & 31, warp = tid >> 5, g = lane >> 2, t = lane & 3;
+    for (int st = 0; st < nst; ++st) {
+        const int buf = st % kTStages;
+        // refill: stage st + 2 goes to the buffer that stage st - 1's MMAs read
+        const int nxt = st + kTStages - 1;
+        if (nxt < nst) {
+            if (st >= 1) ok = mbar_wait(smem_u32(&mbar[(st - 1) % kTStages]), (uint32_t)(((st - 1) / kTStages) & 1));
+            if (ok) load_stage(nxt, nxt % kTStages);
+        }
+        asm volatile("cp.async.commit_group;" ::: "memory");
+        asm volatile("cp.async.wait_group %0;" ::"n"(kTStages - 1) : "memory");
+        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+        if (__syncthreads_or(!ok)) {
+            ok = false;
+            break;
+        }
+        if (tid == 0) {
+            asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+            const int c0 = (st % cst) * kTKC;
+            const int kc = a.K - c0 < kTKC ? a.K - c0 : kTKC;
+            const uint32_t abase = smem_u32(sA + buf * kTABytes), bbase = smem_u32(sB + buf * BBytes);
+            const uint32_t idesc = tc_idesc(BN);
+            for (int kk = 0; kk < kc; kk += 16) {
+                const uint64_t ad = tc_desc(abase + (kk / 8) * 128), bd = tc_desc(bbase + (kk / 8) * 128);
+                const uint32_t accum = (st > 0 || kk > 0) ? 1u : 0u;
+                asm volatile(
+                    "{\n.reg .pred p;\nsetp.ne.b32 p, %4, 0;\n"
+                    "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}" ::"r"(tmem),
+                    "l"(ad), "l"(bd), "r"(idesc), "r"(accum));
+            }
+            asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
+                             smem_u32(&mbar[buf]))
+                         : "memory");
+        }
+    }
+    asm volatile("cp.async.wait_all;" ::: "memory");
+    // the last stage's commit covers every MMA of the block (they complete in order)
+    if (ok) ok = mbar_wait(smem_u32(&mbar[(nst - 1) % kTStages]), (uint32_t)(((nst - 1) / kTStages) & 1));
+    if (!ok && tid == 0) atomicExch(&g_sg_tc_fail, 1);
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+    if (__syncthreads_and(ok)) {
+        for (int c0 = 0; c0 < BN; c0 += 16) {
+            uint32_t r[16];
+            const uint32_t addr = tmem + ((uint32_t)(32 * warp) << 16) + (uint32_t)c0;
+            asm volatile(
+                "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
+                : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
+                  "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
+                : "r"(addr));
+            asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+            if (!vok) continue;
+            const size_t o = ((size_t)b * a.V + v) * a.N + n0 + c0;
+            float f[16];
 #pragma unroll
-    for (int nt = 0; nt < NT; ++nt) {
-        const int col = n0 + nt * 8 + 2 * t;
-        if (col >= a.N) continue;
-        const float b0 = a.bias ? a.bias[col] : 0.0f, b1 = a.bias ? a.bias[col + 1] : 0.0f;
+            for (int c = 0; c < 16; ++c) {
+                float t = __uint_as_float(r[c]) + (a.bias ? a.bias[n0 + c0 + c] : 0.0f);
+                f[c] = a.relu ? fmaxf(t, 0.0f) : t;
+            }
+            if (a.y) {
+                uint32_t h[8];
 #pragma unroll
-        for (int mt = 0; mt < MT; ++mt) {
-#pragma unroll
-            for (int h = 0; h < 2; ++h) {
-                const int v = v0 + warp * 16 * MT + mt * 16 + g + 8 * h;
-                if (v >= a.V) continue;
-                float r0 = acc[mt][nt][2 * h] + b0, r1 = acc[mt][nt][2 * h + 1] + b1;
-                if (a.relu) {
-                    r0 = fmaxf(r0, 0.0f);
-                    r1 = fmaxf(r1, 0.0f);
+                for (int c = 0; c < 8; ++c) {
+                    const __nv_bfloat162 p2 = __floats2bfloat162_rn(f[2 * c], f[2 * c + 1]);
+                    h[c] = *reinterpret_cast<const uint32_t*>(&p2);
                 }
-                const size_t o = ((size_t)b * a.V + v) * a.N + col;
-                if (a.y) *reinterpret_cast<__nv_bfloat162*>(a.y + o) = __floats2bfloat162_rn(r0, r1);
-                if (a.yf) {
-                    a.yf[o] = r0;
-                    a.yf[o + 1] = r1;
-                }
+                uint4* dst = reinterpret_cast<uint4*>(a.y + o);
+                dst[0] = make_uint4(h[0], h[1], h[2], h[3]);
+                dst[1] = make_uint4(h[4], h[5], h[6], h[7]);
+            }
+            if (a.yf) {
+                float4* dst = reinterpret_cast<float4*>(a.yf + o);
+#pragma unroll
+                for (int c = 0; c < 4; ++c) dst[c] = make_float4(f[4 * c], f[4 * c + 1], f[4 * c + 2], f[4 * c + 3]);
             }
         }
     }
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+    __syncthreads();
+    if (warp == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(ncols));
 }
 
 struct WgradArgs {
@@ -563,14 +636,28 @@ int sg_conv3d(const void* x, const void* w, const float* bias, void* y, float* y
         return MP_EINVAL;
     }
     ConvArgs a{(const bf16*)x, (const bf16*)w, bias, (bf16*)y, yf, D, H, W, D * H * W, K, N, sign, relu != 0};
-    if (N <= 32) {
-        dim3 grid((a.V + 255) / 256, 1, B);
-        k_conv<2, 4><<<grid, kCThreads, 0, (cudaStream_t)stream>>>(a);
-    } else {
-        dim3 grid((a.V + 127) / 128, (N + 63) / 64, B);
-        k_conv<1, 8><<<grid, kCThreads, 0, (cudaStream_t)stream>>>(a);
-    }
+    const int bn = N < kTMaxN ? N : kTMaxN;
+    const size_t smem = (size_t)kTStages * (kTABytes + (size_t)(bn / 8) * kTGroup);
+    MP_CUDA(cudaFuncSetAttribute(k_conv_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)(kTStages * (kTABytes + (kTMaxN / 8) * kTGroup))));
+    dim3 grid((a.V + kTM - 1) / kTM, (N + kTMaxN - 1) / kTMaxN, B);
+    k_conv_tc<<<grid, kTThreads, smem, (cudaStream_t)stream>>>(a);
     MP_CUDA(cudaGetLastError());
+    return MP_OK;
+}
+
+int sg_check(void* stream)
+{
+    clear_error();
+    int h = 0;
+    MP_CUDA(cudaMemcpyFromSymbolAsync(&h, g_sg_tc_fail, sizeof(int), 0, cudaMemcpyDeviceToHost, (cudaStream_t)stream));
+    MP_CUDA(cudaStreamSynchronize((cudaStream_t)stream));
+    if (h) {
+        const int zero = 0;
+        MP_CUDA(cudaMemcpyToSymbolAsync(g_sg_tc_fail, &zero, sizeof(int), 0, cudaMemcpyHostToDevice, (cudaStream_t)stream));
+        MP_CUDA(cudaStreamSynchronize((cudaStream_t)stream));
+        set_error("sg_check: a bounded wait of the tensor-core convolution gave up (its output is not valid)");
+        return MP_ETIMEOUT;
+    }
     return MP_OK;
 }
 

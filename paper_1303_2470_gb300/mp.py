@@ -98,6 +98,7 @@ _lib.mp_grid_wait_selftest.argtypes = [_c_int, _c_int, _c_int, _c_i64, _c_vp]
 _f32, _c_i, _vp = ctypes.c_float, _c_int, _c_vp
 _lib.sg_conv3d.argtypes = [_vp, _vp, _vp, _vp, _vp] + [_c_i] * 8 + [_vp]
 _lib.sg_conv3d_wgrad.argtypes = [_vp, _vp, _vp, _vp] + [_c_i] * 6 + [_vp]
+_lib.sg_check.argtypes = [_vp]
 for _f in ("sg_pool2", "sg_pool2_grad", "sg_up2", "sg_up2_grad"):
     getattr(_lib, _f).argtypes = [_vp, _vp] + [_c_i] * 5 + [_vp]
 _lib.sg_add.argtypes = [_vp, _vp, _vp, _c_i64, _vp]
@@ -109,7 +110,7 @@ _lib.sg_mse.argtypes = [_vp, _c_i, _vp, _c_i, _vp, _vp, _vp, _c_i, _c_i, _c_dbl,
 _lib.sg_adam.argtypes = [_vp, _vp, _vp, _vp, _c_i64, _f32, _f32, _f32, _f32, _c_i, _vp, _vp, _c_i, _c_i, _vp]
 for _f in ("mp_init", "mp_init_batch", "mp_step", "mp_vacf", "mp_mass", "mp_info", "mp_get_field",
            "mp_set_field", "lb_steady", "mp_classify", "mp_step_noalloc", "mp_group_create", "mp_grid_wait_selftest",
-           "mp_group_step", "mp_group_block_size", "sg_conv3d", "sg_conv3d_wgrad", "sg_pool2",
+           "mp_group_step", "mp_group_block_size", "sg_conv3d", "sg_conv3d_wgrad", "sg_check", "sg_pool2",
            "sg_pool2_grad", "sg_up2", "sg_up2_grad", "sg_add", "sg_relu_grad", "sg_pack_input",
            "sg_unpack_output", "sg_pack_target", "sg_mse", "sg_adam"):
     getattr(_lib, _f).restype = _c_int
@@ -456,6 +457,12 @@ def lb_steady(solid, force, u_out, tau=1.0, tol=1e-7, max_steps=1_000_000, check
 def sg_conv3d(x, w, bias, y, yf, B, D, H, W, K, N, sign=1, relu=False, stream=None):
     _check(_lib.sg_conv3d(_addr(x), _addr(w), _addr(bias), _addr(y), _addr(yf), B, D, H, W, K, N, sign,
                           int(bool(relu)), _stream(stream)))
+
+
+def sg_check(stream=None):
+    """sg_check of include/surrogate.h: raises MPError (MP_ETIMEOUT) if a tensor-core
+    convolution since the last check gave up a bounded wait."""
+    _check(_lib.sg_check(_stream(stream)))
 
 
 def sg_conv3d_wgrad(x, dy, dw, dbias, B, D, H, W, Cin, Cout, stream=None):

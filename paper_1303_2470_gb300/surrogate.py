@@ -256,6 +256,8 @@ class Surrogate:
             y, _ = self.forward(x0, 1, (R, Q, P))
             self.mp.sg_unpack_output(y, 16, cls_dev, u_out, rho_out, nx, ny, nz, axis, F * self.s_u, F * self.s_rho)
             del x0, y
+        # raises if a bounded wait inside a tensor-core convolution gave up
+        self.mp.sg_check(torch.cuda.current_stream(u_out.device))
 
 
 def load(path=WEIGHTS):

@@ -206,11 +206,15 @@ def test_network_loss_and_gradients_match_autograd(mp):
     assert float((y.cpu() - yr.detach()).abs().max()) <= 2e-2 * float(yr.detach().abs().max())
     assert abs(loss.item() / lr_.item() - 1.0) < 2e-2
     # Each kernel is checked alone above (1e-5); this test checks the wiring (layer order,
-    # skips, pooling, ReLU masks), whose mistakes give errors of order one. Over all
-    # parameters the relative error is bounded by the BF16 stages: a gradient passes at most
-    # 15 forward and 15 backward roundings of 2^-9, 30 x 2^-9 = 5.9 %, so 6 %. Per tensor the
-    # bound is looser (15 %): a bias gradient is a sum over voxels whose terms cancel, so its
-    # rounding error scales with the sum of their magnitudes, not with the sum itself.
+    # skips, pooling, ReLU masks), whose mistakes give errors of order one (a wrong layer,
+    # skip or mask replaces a gradient). Over all parameters the relative error is bounded by
+    # the BF16 stages: a gradient passes at most 15 forward and 15 backward roundings of
+    # 2^-9, 30 x 2^-9 = 5.9 %, so 6 %. Per tensor the bound is looser: a weight or bias
+    # gradient is a sum over voxels whose terms cancel, so its rounding error scales with the
+    # sum of their magnitudes, not with the sum itself, and the weight-gradient and loss
+    # kernels add with atomics, so the BF16 roundings downstream differ from run to run
+    # (measured on GB300 for e2a.W over repeated runs: 4 % to 19 %, with either convolution
+    # kernel). 30 % per tensor still separates those from the errors of order one.
     num, den = 0.0, 0.0
     for name, t in model.p.items():
         for key in ("W", "b"):
@@ -218,9 +222,10 @@ def test_network_loss_and_gradients_match_autograd(mp):
             ref = pr[name + "." + key].grad
             e = float((ours - ref).norm())
             r = float(ref.norm())
-            assert e < 0.15 * r, (name, key, e / r)
+            assert e < 0.30 * r, (name, key, e / r)
             num += e * e
             den += r * r
+    print(f"network gradients: relative error over all parameters {np.sqrt(num / den):.4f}")
     assert np.sqrt(num / den) < 6e-2
 
 
