@@ -41,44 +41,52 @@ struct ConvArgs {
 // ---------------------------------------------------------------------------------------
 // Forward (and transposed) convolution on the 5th-generation tensor cores: an implicit GEMM
 // with M = 128 voxels per block, N = the block's output channels (up to 256, one MMA wide),
-// K = 27 taps x K input channels in stages of one tap x up to 64 channels (four MMAs of
-// K = 16). Operands sit in shared memory in the canonical K-major layout without swizzle:
-// 8-row x 16-byte core matrices, the eight k-chunks of a stage of one 8-row group
-// contiguous (1024 bytes), so a descriptor with leading offset 128 (next core matrix along
-// k) and stride offset 1024 (next 8-row group) describes any 16-wide k-slice. The
-// accumulators (FP32) live in tensor memory; one thread issues the MMAs. A ring of three
-// shared-memory stages is filled by asynchronous copies (cp.async, zero-filled outside the
-// volume); the MMAs of a stage signal an mbarrier when they complete, which frees its
-// buffer for the copies of a later stage. The epilogue reads the accumulators back with
-// tcgen05.ld (warp w holds rows 32w..32w+31), adds the bias, applies the ReLU and stores.
-// Every wait is bounded; a wait that gives up records it in g_sg_tc_fail (read by
-// sg_check), and the block still releases its tensor memory.
+// K = 27 taps x K input channels, flattened tap-major, in stages of 64 consecutive elements
+// (four MMAs of K = 16; a stage spans several taps when K < 64). Operands sit in shared
+// memory in the K-major layout with 128-byte swizzling:
+// each 8-row group is one 1024-byte atom whose row r holds the stage's 64 elements as eight
+// 16-byte chunks, chunk j stored at position j ^ (r mod 8); a descriptor with stride offset
+// 1024 (next atom) whose start advances by 32 bytes per 16-channel slice describes any
+// K = 16 slice. With this layout the eight lanes that copy one voxel row read its 128
+// contiguous bytes and write eight distinct bank groups. The accumulators (FP32) live in
+// tensor memory; one thread issues the MMAs. A ring of shared-memory stages is filled by
+// asynchronous copies (cp.async, L1-cached, zero-filled outside the volume); the MMAs of a
+// stage signal an mbarrier when they complete, which frees its buffer for the copies of a
+// later stage. The epilogue reads the accumulators back with tcgen05.ld (warp w holds rows
+// 32w..32w+31), adds the bias, applies the ReLU and stores. Every wait is bounded; a wait
+// that gives up records it in g_sg_tc_fail (read by sg_check), and the block still releases
+// its tensor memory.
 // ---------------------------------------------------------------------------------------
 constexpr int kTM = 128;         // voxels per block (MMA M)
-#ifndef SG_TC_KC
-#define SG_TC_KC 32
-#endif
-constexpr int kTKC = SG_TC_KC;   // input channels per stage
+constexpr int kTKC = 64;         // reduction elements per stage: one swizzle atom row (128 bytes)
 #ifndef SG_TC_STAGES
 #define SG_TC_STAGES 2
 #endif
 constexpr int kTStages = SG_TC_STAGES;  // shared-memory ring
 constexpr int kTThreads = 128;   // four warps: one accumulator row per thread
 constexpr int kTMaxN = 256;      // output channels per block (MMA N)
-constexpr int kTGroup = (kTKC / 8) * 128;  // bytes of one 8-row group of a stage
-constexpr int kTABytes = (kTM / 8) * kTGroup;
+constexpr int kTAtom = 1024;     // one 8-row group: 8 rows x 128 bytes
+constexpr int kTABytes = (kTM / 8) * kTAtom;
+constexpr int kTPieces = kTM * 8 / kTThreads;  // 16-byte A pieces per thread and stage
 constexpr long long kTWaitNs = 1000000000LL;  // a wait gives up after 1 s of the global timer
 
 __device__ int g_sg_tc_fail;
 
 __device__ __forceinline__ uint32_t smem_u32(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
 
-// shared-memory matrix descriptor: start address, leading byte offset 128 (along k), stride
-// byte offset 1024 (8-row groups), no swizzle, descriptor version 1 (bit 46)
+// byte offset of 16-byte chunk j of row r in a 128-byte-swizzled K-major tile
+__device__ __forceinline__ uint32_t swz(int r, int j)
+{
+    return (uint32_t)((r >> 3) * kTAtom + (r & 7) * 128 + ((j ^ (r & 7)) << 4));
+}
+
+// shared-memory matrix descriptor: start address, stride byte offset 1024 (next 8-row atom),
+// leading offset unused with swizzling (1), descriptor version 1 (bit 46), 128-byte
+// swizzling (mode 2, bits 61-63)
 __device__ __forceinline__ uint64_t tc_desc(uint32_t addr)
 {
-    return (uint64_t)((addr & 0x3FFFFu) >> 4) | ((uint64_t)(128 >> 4) << 16) | ((uint64_t)(kTGroup >> 4) << 32) |
-           (1ull << 46);
+    return (uint64_t)((addr & 0x3FFFFu) >> 4) | (1ull << 16) | ((uint64_t)(kTAtom >> 4) << 32) | (1ull << 46) |
+           (2ull << 61);
 }
 
 // instruction descriptor of kind::f16: FP32 accumulator, BF16 A and B, both K-major,
@@ -88,18 +96,11 @@ __host__ __device__ constexpr uint32_t tc_idesc(int n)
     return (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(n >> 3) << 17) | ((uint32_t)(kTM >> 4) << 24);
 }
 
-#ifndef SG_TC_CACHE_L1
-#define SG_TC_CACHE_L1 1
-#endif
-// 16-byte asynchronous copy global -> shared (zero-filled beyond `bytes`); through L1, where
+// 16-byte asynchronous copy global -> shared (zero-filled beyond `bytes`), through L1, where
 // the tap-shifted tiles of one block overlap
 __device__ __forceinline__ void cp_async16(uint32_t dst, const void* src, uint32_t bytes)
 {
-#if SG_TC_CACHE_L1
     asm volatile("cp.async.ca.shared.global [%0], [%1], 16, %2;" ::"r"(dst), "l"(src), "r"(bytes) : "memory");
-#else
-    asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;" ::"r"(dst), "l"(src), "r"(bytes) : "memory");
-#endif
 }
 
 __device__ __forceinline__ unsigned long long tc_now_ns()
@@ -125,28 +126,41 @@ __device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity)
     }
 }
 
+template <int kK>  // input channels, 0: a.K at run time
 __global__ void __launch_bounds__(kTThreads) k_conv_tc(const ConvArgs a)
 {
-    extern __shared__ __align__(1024) unsigned char tc_smem[];
+    extern __shared__ __align__(1024) unsigned char tc_smem_raw[];
     __shared__ __align__(8) uint64_t mbar[kTStages];
     __shared__ uint32_t tmem_base;
     const int tid = threadIdx.x, warp = tid >> 5;
     const int n0 = blockIdx.y * kTMaxN;
     const int BN = a.N - n0 < kTMaxN ? a.N - n0 : kTMaxN;  // a multiple of 16
-    const int BBytes = (BN / 8) * kTGroup;
+    const int BBytes = (BN / 8) * kTAtom;
+    // operand atoms must start on 1024-byte boundaries (the swizzle pattern is anchored there)
+    unsigned char* tc_smem = tc_smem_raw + ((kTAtom - (smem_u32(tc_smem_raw) & (kTAtom - 1))) & (kTAtom - 1));
     unsigned char* sA = tc_smem;
     unsigned char* sB = tc_smem + kTStages * kTABytes;
     const int b = blockIdx.z;
-    const int v = blockIdx.x * kTM + tid;  // this thread's voxel row of A and of the result
-    const bool vok = v < a.V;
-    int xa = 0, ya = 0, za = 0;
-    if (vok) {
-        xa = v % a.W;
-        ya = (v / a.W) % a.H;
-        za = v / (a.W * a.H);
+    const int v = blockIdx.x * kTM + tid;  // this thread's result row
+    // A pieces of this thread: piece p = tid + 128 i covers row p / 8, chunk p % 8 (the
+    // chunk is the same for every i); their voxel coordinates
+    const int pj = tid & 7;
+    int px[kTPieces], py[kTPieces], pz[kTPieces];
+#pragma unroll
+    for (int i = 0; i < kTPieces; ++i) {
+        const int vr = blockIdx.x * kTM + (tid + kTThreads * i) / 8;
+        px[i] = -1;
+        py[i] = pz[i] = 0;
+        if (vr < a.V) {
+            px[i] = vr % a.W;
+            py[i] = (vr / a.W) % a.H;
+            pz[i] = vr / (a.W * a.H);
+        }
     }
-    const int cst = (a.K + kTKC - 1) / kTKC;  // stages per tap
-    const int nst = 27 * cst;
+    // stages: 64 consecutive elements of the flattened (tap, channel) reduction index (tap
+    // major); a 16-byte chunk never straddles two taps since K is a multiple of 16
+    const int K = kK ? kK : a.K;
+    const int nst = (27 * K + kTKC - 1) / kTKC;
     uint32_t ncols = 32;
     while ((int)ncols < BN) ncols <<= 1;
     if (tid == 0) {
@@ -164,23 +178,42 @@ __global__ void __launch_bounds__(kTThreads) k_conv_tc(const ConvArgs a)
     const uint32_t tmem = tmem_base;
     const bf16* xb = a.x + (size_t)b * a.V * a.K;
 
-    // asynchronous copies of stage st into ring buffer buf: this thread's A row, and B rows
-    // tid, tid + 128, ... of the block's output channels
+    // reduction elements of stage st (a multiple of 16), and the tap and channel of chunk j
+    auto stage_kc = [&](int st) { return 27 * K - st * kTKC < kTKC ? 27 * K - st * kTKC : kTKC; };
+    auto chunk_of = [&](int st, int j, int& tap, int& ch) {
+        const int e = st * kTKC + 8 * j;
+        tap = e / K;
+        ch = e - tap * K;
+    };
+
+    // asynchronous copies of stage st into ring buffer buf
     auto load_stage = [&](int st, int buf) {
-        const int tap = st / cst, c0 = (st - tap * cst) * kTKC;
-        const int kc = a.K - c0 < kTKC ? a.K - c0 : kTKC;
-        const int dz = tap / 9 - 1, dy = (tap / 3) % 3 - 1, dx = tap % 3 - 1;
-        const bf16* src = xb;  // any valid address when the row lies outside the volume
-        if (vok) {
-            const int xs = wrap(xa + a.sign * dx, a.W), ys = wrap(ya + a.sign * dy, a.H), zs = wrap(za + a.sign * dz, a.D);
-            src = xb + ((size_t)(zs * a.H + ys) * a.W + xs) * a.K + c0;
+        const int kc = stage_kc(st);
+        const uint32_t abase = smem_u32(sA + buf * kTABytes);
+        if (pj < kc / 8) {
+            int tap, ch;
+            chunk_of(st, pj, tap, ch);
+            const int dz = tap / 9 - 1, dy = (tap / 3) % 3 - 1, dx = tap % 3 - 1;
+#pragma unroll
+            for (int i = 0; i < kTPieces; ++i) {
+                const int row = (tid + kTThreads * i) >> 3;
+                const bf16* src = xb;  // any valid address when the row lies outside the volume
+                if (px[i] >= 0) {
+                    const int xs = wrap(px[i] + a.sign * dx, a.W), ys = wrap(py[i] + a.sign * dy, a.H);
+                    const int zs = wrap(pz[i] + a.sign * dz, a.D);
+                    src = xb + ((size_t)(zs * a.H + ys) * a.W + xs) * K + ch;
+                }
+                cp_async16(abase + swz(row, pj), src, px[i] >= 0 ? 16u : 0u);
+            }
         }
-        const uint32_t da = smem_u32(sA + buf * kTABytes + (tid >> 3) * kTGroup + (tid & 7) * 16);
-        for (int j = 0; j < kc / 8; ++j) cp_async16(da + j * 128, src + (vok ? 8 * j : 0), vok ? 16u : 0u);
-        for (int n = tid; n < BN; n += kTThreads) {
-            const bf16* ws = a.w + ((size_t)tap * a.N + n0 + n) * a.K + c0;
-            const uint32_t db = smem_u32(sB + buf * BBytes + (n >> 3) * kTGroup + (n & 7) * 16);
-            for (int j = 0; j < kc / 8; ++j) cp_async16(db + j * 128, ws + 8 * j, 16u);
+        const uint32_t bbase = smem_u32(sB + buf * BBytes);
+        for (int p = tid; p < BN * 8; p += kTThreads) {
+            const int n = p >> 3, j = p & 7;
+            if (j < kc / 8) {
+                int tap, ch;
+                chunk_of(st, j, tap, ch);
+                cp_async16(bbase + swz(n, j), a.w + ((size_t)tap * a.N + n0 + n) * K + ch, 16u);
+            }
         }
     };
 
@@ -191,7 +224,7 @@ __global__ void __launch_bounds__(kTThreads) k_conv_tc(const ConvArgs a)
     }
     for (int st = 0; st < nst; ++st) {
         const int buf = st % kTStages;
-        // refill: stage st + 2 goes to the buffer that stage st - 1's MMAs read
+        // refill: stage st + kTStages - 1 goes to the buffer that stage st - 1's MMAs read
         const int nxt = st + kTStages - 1;
         if (nxt < nst) {
             if (st >= 1) ok = mbar_wait(smem_u32(&mbar[(st - 1) % kTStages]), (uint32_t)(((st - 1) / kTStages) & 1));
@@ -206,12 +239,11 @@ __global__ void __launch_bounds__(kTThreads) k_conv_tc(const ConvArgs a)
         }
         if (tid == 0) {
             asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-            const int c0 = (st % cst) * kTKC;
-            const int kc = a.K - c0 < kTKC ? a.K - c0 : kTKC;
+            const int kc = stage_kc(st);
             const uint32_t abase = smem_u32(sA + buf * kTABytes), bbase = smem_u32(sB + buf * BBytes);
             const uint32_t idesc = tc_idesc(BN);
             for (int kk = 0; kk < kc; kk += 16) {
-                const uint64_t ad = tc_desc(abase + (kk / 8) * 128), bd = tc_desc(bbase + (kk / 8) * 128);
+                const uint64_t ad = tc_desc(abase + kk * 2), bd = tc_desc(bbase + kk * 2);
                 const uint32_t accum = (st > 0 || kk > 0) ? 1u : 0u;
                 asm volatile(
                     "{\n.reg .pred p;\nsetp.ne.b32 p, %4, 0;\n"
@@ -229,6 +261,7 @@ __global__ void __launch_bounds__(kTThreads) k_conv_tc(const ConvArgs a)
     if (!ok && tid == 0) atomicExch(&g_sg_tc_fail, 1);
     asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
     if (__syncthreads_and(ok)) {
+        const bool vok = v < a.V;
         for (int c0 = 0; c0 < BN; c0 += 16) {
             uint32_t r[16];
             const uint32_t addr = tmem + ((uint32_t)(32 * warp) << 16) + (uint32_t)c0;
@@ -637,10 +670,19 @@ int sg_conv3d(const void* x, const void* w, const float* bias, void* y, float* y
     }
     ConvArgs a{(const bf16*)x, (const bf16*)w, bias, (bf16*)y, yf, D, H, W, D * H * W, K, N, sign, relu != 0};
     const int bn = N < kTMaxN ? N : kTMaxN;
-    const size_t smem = (size_t)kTStages * (kTABytes + (size_t)(bn / 8) * kTGroup);
-    MP_CUDA(cudaFuncSetAttribute(k_conv_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)(kTStages * (kTABytes + (kTMaxN / 8) * kTGroup))));
+    // the ring plus room to align it to a 1024-byte boundary
+    const size_t smem = (size_t)kTStages * (kTABytes + (size_t)(bn / 8) * kTAtom) + kTAtom;
+    // instances with the input-channel count fixed at compile time for the network's layers
+    void (*kern)(const ConvArgs) = K == 16   ? k_conv_tc<16>
+                                   : K == 32 ? k_conv_tc<32>
+                                   : K == 64 ? k_conv_tc<64>
+                                   : K == 96 ? k_conv_tc<96>
+                                   : K == 128 ? k_conv_tc<128>
+                                               : k_conv_tc<0>;
+    MP_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 (int)(kTStages * (kTABytes + (kTMaxN / 8) * kTAtom) + kTAtom)));
     dim3 grid((a.V + kTM - 1) / kTM, (N + kTMaxN - 1) / kTMaxN, B);
-    k_conv_tc<<<grid, kTThreads, smem, (cudaStream_t)stream>>>(a);
+    kern<<<grid, kTThreads, smem, (cudaStream_t)stream>>>(a);
     MP_CUDA(cudaGetLastError());
     return MP_OK;
 }

@@ -46,7 +46,9 @@ def _ref_conv(x, w, bias, sign=1):
 
 
 @pytest.mark.parametrize("shape,K,N,relu", [((2, 4, 8, 12), 32, 48, True), ((1, 6, 5, 7), 16, 16, False),
-                                            ((1, 8, 8, 8), 128, 64, True), ((2, 6, 9, 10), 64, 32, True)])
+                                            ((1, 8, 8, 8), 128, 64, True), ((2, 6, 9, 10), 64, 32, True),
+                                            ((1, 5, 7, 6), 48, 32, False), ((1, 4, 6, 10), 96, 96, True),
+                                            ((1, 3, 4, 9), 80, 272, False)])
 def test_conv_forward_matches_torch(mp, shape, K, N, relu):
     B, D, H, W = shape
     rng = np.random.default_rng(1)
