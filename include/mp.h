@@ -104,7 +104,8 @@ typedef struct {
     int autotune;       /* MP_SCHEME_DIRECT only. 0: run the variant given below. Nonzero:
                            mp_init times every variant (link table or link terms recomputed
                            from the flow; one launch per step or one persistent launch per run
-                           of steps; blocks of 128, 256 or 512) for 20 steps on the initial
+                           of steps; blocks of 128, 256 or 512; several species also tiled)
+                           for 20 steps on the initial
                            state, restores the state and keeps the fastest (needs 24 free
                            entries in the series). See mp_variant.                          */
     int variant;        /* MP_SCHEME_DIRECT without autotune: 0 (one launch per step, link
@@ -116,6 +117,9 @@ typedef struct {
 #define MP_VARIANT_PERSISTENT 2 /* one persistent launch per run of steps                       */
 #define MP_VARIANT_BLOCK128 4   /* blocks of 128 threads (default 256)                          */
 #define MP_VARIANT_BLOCK512 8   /* blocks of 512 threads                                        */
+#define MP_VARIANT_TILED 16     /* several species: tiles of 32 x 8 lattice columns marched along
+                                   z through shared memory (blocks of 128, link terms recomputed);
+                                   ignored by contexts of one species                          */
 
 void mp_default_options(mp_options* opt);
 

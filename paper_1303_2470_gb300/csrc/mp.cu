@@ -139,6 +139,7 @@ struct Args {
     int SP;  // species, padded to a whole number of chunks (1 for one species)
     int SC;  // species per chunk (1 for one species, else 8 / FP); element (n, s, f) sits at
              // (((s / SC) * rows + n) * SC + s % SC) * FP + f, rows = N for P, NI for P_ads
+    int compact;  // P over the fluid list: row = work item k, rows = NF
     Div dx, dxy;  // division by nx and by nx*ny
     const uint32_t* iface;
     const int32_t* ibase;
@@ -674,6 +675,8 @@ __global__ void __launch_bounds__(kThreads)
     const bool active = k < a.NF;
     Node<T> d;
     if (active) load_node<T>(a, k, d);
+    const size_t prows = a.compact ? (size_t)a.NF : (size_t)a.N;
+    const size_t prow = a.compact ? (size_t)k : (size_t)d.n;
     const int K2 = 2 * a.S * a.M;
     for (int sp = 0; sp < a.S; ++sp) {
         const T hl = a.hl[sp], pa = a.pa[sp], pd = a.pd[sp];
@@ -700,7 +703,7 @@ __global__ void __launch_bounds__(kThreads)
                 xn += pd * xa0;
                 A1[ai] = Narrow<TS>::one((pa * x0 + (T(1) - pd) * xa0) * sc, 0u, false);
             }
-            P1[elem(a, a.N, d.n, sp, 0)] = Narrow<TS>::one(xn * sc, 0u, false);
+            P1[elem(a, prows, prow, sp, 0)] = Narrow<TS>::one(xn * sc, 0u, false);
 #pragma unroll
             for (int m = 0; m < kMaxF - 1; ++m) {
                 if (m < a.M) {
@@ -710,7 +713,7 @@ __global__ void __launch_bounds__(kThreads)
                     for (int i = 1; i < kQ; ++i)
                         if (ci(i, g) != 0) pg += pin[i] * T(ci(i, g));
                     pg *= invZ;
-                    P1[elem(a, a.N, d.n, sp, 1 + m)] = Narrow<TS>::one(pg * sc, 0u, false);
+                    P1[elem(a, prows, prow, sp, 1 + m)] = Narrow<TS>::one(pg * sc, 0u, false);
                     if (d.itf) A1[elem(a, a.NI, d.aidx, sp, 1 + m)] = Narrow<TS>::one(T(0), 0u, false);
                     T us, us2;
                     mean_step(pout, g, us, us2);
@@ -772,7 +775,7 @@ __global__ void __launch_bounds__(kThreads)
     double v[3] = {0.0, 0.0, 0.0};
     if (k < a.NF) {
         const int n = __ldg(a.flist + k);
-        v[0] = (double)widen1(P[elem(a, a.N, n, sp, 0)]);
+        v[0] = (double)widen1(P[a.compact ? elem(a, a.NF, k, sp, 0) : elem(a, a.N, n, sp, 0)]);
         const uint32_t bits = __ldg(a.iface + (n >> 5));
         if ((bits >> (n & 31)) & 1u) {
             const int j = __ldg(a.ibase + (n >> 5)) + __popc(bits & ((1u << (n & 31)) - 1u));
@@ -854,6 +857,7 @@ Args<T> make_args(const mp_ctx* c)
     a.FP = c->FP;
     a.SP = c->SP;
     a.SC = c->SC;
+    a.compact = c->compact ? 1 : 0;
     a.dx = make_div((unsigned)c->geo.nx);
     a.dxy = make_div((unsigned)(c->geo.nx * c->geo.ny));
     a.iface = c->geo.iface;
@@ -923,7 +927,7 @@ int init_typed(mp_ctx* c, const float* u_in, int init_density)
     const int chunk = 8 / c->FP;  // species per 32-byte chunk of a node record
     c->SP = c->S == 1 ? 1 : (c->S + chunk - 1) / chunk * chunk;
     c->SC = c->S == 1 ? 1 : chunk;
-    const size_t fieldN = (size_t)c->SP * N * c->FP;
+    const size_t fieldN = (size_t)c->SP * (c->compact ? (size_t)c->geo.n_fluid : (size_t)N) * c->FP;
     const size_t fieldA = (size_t)c->SP * NI * c->FP;
     const int Kser = c->S * c->M;
     c->elem = sizeof(TS);
@@ -1113,7 +1117,7 @@ int mp_init_batch(mp_ctx** out, const mp_geometry* g, const float* u, int n_spec
         set_error("scheme must be MP_SCHEME_FLUX or MP_SCHEME_DIRECT");
         return MP_EINVAL;
     }
-    if (opt.variant < 0 || opt.variant > 15 || (opt.variant & 12) == 12) {
+    if (opt.variant < 0 || opt.variant > 31 || (opt.variant & 12) == 12) {
         set_error("variant must combine MP_VARIANT_* flags (one block size at most)");
         return MP_EINVAL;
     }
@@ -1192,6 +1196,18 @@ int mp_init_batch(mp_ctx** out, const mp_geometry* g, const float* u, int n_spec
         if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
         if (e != cudaSuccess) {
             rc = cuda_fail(e, "interface list copy");
+            destroy(c);
+            return rc;
+        }
+    }
+    c->compact = c->scheme == MP_SCHEME_DIRECT && c->S > 1;
+    if (c->compact) {
+        c->hflist.resize((size_t)c->geo.n_fluid);
+        cudaError_t e = cudaMemcpyAsync(c->hflist.data(), c->geo.flist, sizeof(int32_t) * c->hflist.size(),
+                                        cudaMemcpyDeviceToHost, c->stream);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
+        if (e != cudaSuccess) {
+            rc = cuda_fail(e, "fluid list copy");
             destroy(c);
             return rc;
         }
@@ -1314,20 +1330,26 @@ int mp_get_field(mp_ctx* c, int species, int field, double* free_dense, double* 
     const size_t N = (size_t)c->geo.N;
     const size_t NI = (size_t)(c->geo.n_iface > 0 ? c->geo.n_iface : 1);
     const size_t FP = (size_t)c->FP, SP = (size_t)c->SP, E = c->elem;
-    std::vector<char> buf(N * SP * FP * E), abuf(NI * SP * FP * E);
+    const size_t rowsP = c->compact ? c->hflist.size() : N;
+    std::vector<char> buf(rowsP * SP * FP * E), abuf(NI * SP * FP * E);
     MP_CUDA(cudaMemcpyAsync(buf.data(), c->P[c->cur], buf.size(), cudaMemcpyDeviceToHost, c->stream));
     MP_CUDA(cudaMemcpyAsync(abuf.data(), c->A[c->cur], abuf.size(), cudaMemcpyDeviceToHost, c->stream));
     MP_CUDA(cudaStreamSynchronize(c->stream));
     const size_t SC = (size_t)c->SC;
     const double zsc = c->zsc[species];
     auto at = [&](const std::vector<char>& v, size_t i) {
-        const size_t rows = &v == &buf ? N : NI;
+        const size_t rows = &v == &buf ? rowsP : NI;
         const size_t j = ((((size_t)species / SC) * rows + i) * SC + (size_t)species % SC) * FP + (size_t)field;
         if (E == 8) return ((const double*)v.data())[j];
         if (E == 4) return (double)((const float*)v.data())[j];
         return (double)__half2float(((const __half*)v.data())[j]) * zsc;
     };
-    for (size_t n = 0; n < N; ++n) free_dense[n] = at(buf, n);
+    if (c->compact) {
+        for (size_t n = 0; n < N; ++n) free_dense[n] = 0.0;
+        for (size_t k = 0; k < rowsP; ++k) free_dense[c->hflist[k]] = at(buf, k);
+    } else {
+        for (size_t n = 0; n < N; ++n) free_dense[n] = at(buf, n);
+    }
     if (ads_dense) {
         for (size_t n = 0; n < N; ++n) ads_dense[n] = 0.0;
         for (size_t k = 0; k < c->ilist.size(); ++k) ads_dense[c->ilist[k]] = at(abuf, k);
@@ -1347,8 +1369,9 @@ int mp_set_field(mp_ctx* c, int species, int field, const double* free_dense, co
     const size_t NI = (size_t)(c->geo.n_iface > 0 ? c->geo.n_iface : 1);
     const size_t FP = (size_t)c->FP, SP = (size_t)c->SP, E = c->elem;
     // read the node records, replace one species' field, write them back; solids stay zero
+    const size_t rowsP = c->compact ? c->hflist.size() : N;
     std::vector<uint32_t> fl((size_t)c->geo.W);
-    std::vector<char> buf(N * SP * FP * E), abuf(NI * SP * FP * E);
+    std::vector<char> buf(rowsP * SP * FP * E), abuf(NI * SP * FP * E);
     MP_CUDA(cudaMemcpyAsync(fl.data(), c->geo.fluid, fl.size() * 4, cudaMemcpyDeviceToHost, c->stream));
     MP_CUDA(cudaMemcpyAsync(buf.data(), c->P[c->cur], buf.size(), cudaMemcpyDeviceToHost, c->stream));
     MP_CUDA(cudaMemcpyAsync(abuf.data(), c->A[c->cur], abuf.size(), cudaMemcpyDeviceToHost, c->stream));
@@ -1356,7 +1379,7 @@ int mp_set_field(mp_ctx* c, int species, int field, const double* free_dense, co
     const size_t SC = (size_t)c->SC;
     const double zsc = c->zsc[species];
     auto put = [&](std::vector<char>& v, size_t i, double x) {
-        const size_t rows = &v == &buf ? N : NI;
+        const size_t rows = &v == &buf ? rowsP : NI;
         const size_t j = ((((size_t)species / SC) * rows + i) * SC + (size_t)species % SC) * FP + (size_t)field;
         if (E == 8)
             ((double*)v.data())[j] = x;
@@ -1365,7 +1388,11 @@ int mp_set_field(mp_ctx* c, int species, int field, const double* free_dense, co
         else
             ((__half*)v.data())[j] = __float2half_rn((float)(x / zsc));
     };
-    for (size_t n = 0; n < N; ++n) put(buf, n, ((fl[n >> 5] >> (n & 31)) & 1u) ? free_dense[n] : 0.0);
+    if (c->compact) {
+        for (size_t k = 0; k < rowsP; ++k) put(buf, k, free_dense[c->hflist[k]]);
+    } else {
+        for (size_t n = 0; n < N; ++n) put(buf, n, ((fl[n >> 5] >> (n & 31)) & 1u) ? free_dense[n] : 0.0);
+    }
     for (size_t k = 0; k < c->ilist.size(); ++k) put(abuf, k, ads_dense ? ads_dense[c->ilist[k]] : 0.0);
     MP_CUDA(cudaMemcpyAsync(c->P[c->cur], buf.data(), buf.size(), cudaMemcpyHostToDevice, c->stream));
     MP_CUDA(cudaMemcpyAsync(c->A[c->cur], abuf.data(), abuf.size(), cudaMemcpyHostToDevice, c->stream));

@@ -43,6 +43,10 @@ struct mp_ctx {
     int FP = 2;  // fields per species record (F padded to 2 or 4)
     int SP = 1;  // species padded to whole chunks (1 for one species)
     int SC = 1;  // species per chunk
+    // free fields stored over the fluid list only ([chunk][k][record], k the index in the
+    // sorted fluid list) instead of over every lattice node: direct scheme, several species
+    bool compact = false;
+    std::vector<int32_t> hflist;  // host copy of the fluid list (field I/O of compact fields)
     mp_group* owner = nullptr;  // set while the context steps as part of a group
     double zsc[MP_MAX_SPECIES] = {};  // stored value x zsc = field value (binary16 storage)
     int stochastic = 1;               // binary16 rounding: stochastic (1) or to nearest (0)

@@ -45,6 +45,11 @@ struct DirectTables {
     float* tab = nullptr;     // incoming p_i (one species) or q_i (several), warp-blocked (tab_at)
     float* own = nullptr;     // [NF][OW] per-node record, see k_direct_tables
     int OW = 0;               // floats per node record
+    // several species (fields over the fluid list): {fluid bits, fluid nodes before the
+    // word} per 32-node word, and the flow vector of every fluid node in list order
+    uint2* fw = nullptr;
+    uint2* iw = nullptr;  // {interface bits, interfacial nodes before the word} per word
+    Flow4<float>* uc = nullptr;
 };
 
 namespace {
@@ -77,12 +82,16 @@ struct DArgs {
     int dir[3];
     int in0;  // buffer read at phase 0
     int nvb;  // virtual blocks of this context
+    int ntx, nty, tz;  // tiled variant: tiles along x and y, planes per tile
     const int32_t* flist;
     const uint32_t* fmask;  // open-link mask of each fluid node (bit i-1: source r - c_i is fluid)
     const int32_t* aidx;
     const float* tab;
     const float* own;
     const Flow4<float>* u4;
+    const uint2* fw;          // several species: fluid bits and prefix per 32-node word
+    const uint2* iw;          // several species: interface bits and prefix per 32-node word
+    const Flow4<float>* uc;   // several species: flow of each fluid node, list order
     float* P[2];
     float* A[2];
     float whf[MP_MAX_SPECIES], whe[MP_MAX_SPECIES], pa[MP_MAX_SPECIES], pd[MP_MAX_SPECIES];
@@ -309,9 +318,34 @@ __device__ __forceinline__ void reduce_zacc(double (*s_red)[kMaxSeries], int M, 
     block_store<kB>(s_red, M, out, accumulate);
 }
 
-// Several species: fields chunk-major, [chunk][node][8 floats] with 8/FP species per chunk.
-// The link loop is outermost within a pass of up to two chunks: q_i is read (or recomputed)
-// once per link and serves every species of both chunks.
+// Index of fluid node s in the sorted fluid list: fluid nodes before its 32-node word plus
+// those below it within the word.
+__device__ __forceinline__ int fluid_index(const uint2* __restrict__ fw, int s)
+{
+    const uint2 w = __ldg(fw + (s >> 5));
+    return (int)w.y + __popc(w.x & ((1u << (s & 31)) - 1u));
+}
+
+// The sources r - c_i lie in nine lattice rows (fixed y and z) around r: r's own row
+// (links 1, 2) and eight others, row j holding the source of link row_centre(j) (c_x = 0)
+// and, for four of them, the sources at x - 1 (link with c_x = +1) and x + 1 (c_x = -1).
+// Fluid nodes of a row are consecutive in the fluid list, so one located centre per row
+// gives the indices of its x - 1 and x + 1 neighbours.
+__host__ __device__ constexpr int row_of(int i)
+{
+    constexpr int t[kQ] = {-1, -1, -1, 0, 1, 0, 1, 1, 0, 2, 2, 2, 4, 5, 3, 3, 3, 6, 7};
+    return t[i];
+}
+__host__ __device__ constexpr int row_centre(int j)
+{
+    constexpr int t[8] = {3, 4, 9, 14, 12, 13, 17, 18};
+    return t[j];
+}
+
+// Several species: fields chunk-major over the fluid list, [chunk][k][8 floats] with 8/FP
+// species per chunk (k = index in the sorted fluid list = work item). The link loop is
+// outermost within a pass of up to two chunks: q_i is read (or recomputed) once per link and
+// serves every species of both chunks. Sources are located in the fluid list by row (above).
 template <int FP, bool kTable, bool kCoherent, int kB>
 __device__ __forceinline__ void vblock_multi(const DArgs& a, int vb, int in, double* part, bool acc_part,
                                              double (*s_red)[kMaxSeries], const float* s_whf, const float* s_whe,
@@ -329,16 +363,22 @@ __device__ __forceinline__ void vblock_multi(const DArgs& a, int vb, int in, dou
     const int k = vb * kB + threadIdx.x;
     const bool active = k < a.NF;
     const int M = a.M, K = a.K;
-    const size_t N = (size_t)a.N, NI = (size_t)a.NI;
-    int n = 0, ai = -1;
+    const size_t NF = (size_t)a.NF, NI = (size_t)a.NI;
+    int ai = -1;
     uint32_t mask = 0;
     Nbr b{};
+    int C[8];  // fluid-list index of each row centre (or of the first fluid node after it)
+    bool xlo = true, xhi = true;  // x - 1 and x + 1 lie in r's row without wrapping
     const float4* o = reinterpret_cast<const float4*>(a.own) + (size_t)(active ? k : 0) * kOW4;
     if (active) {
-        n = ld_stream(a.flist + k);
+        const int n = ld_stream(a.flist + k);
         mask = ld_stream(a.fmask + k);
         ai = ld_stream(a.aidx + k);
         b = nbrs_of(a.nx, a.ny, a.nz, a.dx, a.dxy, n);
+#pragma unroll
+        for (int j = 0; j < 8; ++j) C[j] = fluid_index(a.fw, src_of(b, row_centre(j)));
+        xlo = b.oxm == -1;
+        xhi = b.oxp == 1;
     }
     const int cpn = a.SP / kSC;
 #pragma unroll 1
@@ -355,18 +395,29 @@ __device__ __forceinline__ void vblock_multi(const DArgs& a, int vb, int in, dou
 #pragma unroll
             for (int i = 1; i < kQ; ++i) {
                 if (!((mask >> (i - 1)) & 1u)) continue;
-                const int s = src_of(b, i);
+                const int row = row_of(i);
+                // fluid-list index of the source: the row's centre, or its x -/+ 1 neighbour
+                // (own row: k -/+ 1); located directly where x - 1 or x + 1 wraps around
+                const int base = row < 0 ? k : C[row < 0 ? 0 : row];
+                int s;
+                if (cx(i) == 0)
+                    s = base;
+                else if (cx(i) > 0)
+                    s = xlo ? base - 1 : fluid_index(a.fw, src_of(b, i));
+                else
+                    s = xhi ? base + (row < 0 ? 1 : (int)((mask >> (row_centre(row < 0 ? 0 : row) - 1)) & 1u))
+                            : fluid_index(a.fw, src_of(b, i));
                 float q;
                 if constexpr (kTable) {
                     q = ld_stream(a.tab + tab_at(k, i));
                 } else {
-                    const Flow4<float> uf = ld_flow(a.u4 + s);
+                    const Flow4<float> uf = ld_flow(a.uc + s);
                     q = qlink(edot<float>(i, uf.x, uf.y, uf.z), uf.w);
                 }
 #pragma unroll
                 for (int cc = 0; cc < kCP; ++cc) {
                     if (cc < nc) {
-                        const VC xs = ld_field<kCoherent, 8>(Pin + (size_t)(c0 + cc) * N + s);
+                        const VC xs = ld_field<kCoherent, 8>(Pin + (size_t)(c0 + cc) * NF + s);
 #pragma unroll
                         for (int qq = 0; qq < kSC; ++qq) {
                             const int sp = (c0 + cc) * kSC + qq;
@@ -385,7 +436,7 @@ __device__ __forceinline__ void vblock_multi(const DArgs& a, int vb, int in, dou
 #pragma unroll
             for (int j = 0; j < kSC * 3; ++j) zv[j] = 0.f;
             if (active && cc < nc) {
-                const VC xr = ld_field<kCoherent, 8>(Pin + (size_t)(c0 + cc) * N + n);
+                const VC xr = ld_field<kCoherent, 8>(Pin + (size_t)(c0 + cc) * NF + k);
                 const float4 o0 = __ldg(o);
                 VC xn;
 #pragma unroll
@@ -419,7 +470,7 @@ __device__ __forceinline__ void vblock_multi(const DArgs& a, int vb, int in, dou
                     }
                     st_field<8>(Aout + ia, xan);
                 }
-                st_field<8>(Pout + (size_t)(c0 + cc) * N + n, xn);
+                st_field<8>(Pout + (size_t)(c0 + cc) * NF + k, xn);
 #pragma unroll
                 for (int qq = 0; qq < kSC; ++qq) {
                     const int sp = (c0 + cc) * kSC + qq;
@@ -454,6 +505,297 @@ __device__ __forceinline__ void vblock_multi(const DArgs& a, int vb, int in, dou
     block_store<kB>(s_red, K, part, acc_part);
 }
 
+// ---------------------------------------------------------------------------------------
+// Several species, tiled: a virtual block is a tile of 32 x kRows lattice columns (x, y)
+// over a segment of planes z0 .. z1 - 1 (kRows = 2 per warp). The block marches along z with
+// a ring of four planes of the tile plus a one-node halo in x and y in shared memory: per
+// position the 32-byte field chunk and the flow vector of the node (if fluid) and its
+// fluid-list index (-1 if solid), filled by asynchronous 16-byte copies through L2 two planes
+// ahead of the plane being computed. Each warp owns two rows of the tile; their fluid nodes
+// are packed onto its lanes, and every open link reads its source from shared memory. The
+// per-node arithmetic is that of vblock_multi (same link order and roundings), so the fields
+// are bitwise the same; the Z terms are summed over a warp per plane (FP32) and over the
+// planes in FP64. Several chunks of species: one march per chunk.
+// ---------------------------------------------------------------------------------------
+constexpr int kTileX = 32;
+constexpr int kTilePX = kTileX + 2;
+// ring slots: 4 = copies of plane z + 2 in flight while plane z is computed; 3 = copies
+// issued after plane z is computed (less shared memory, more blocks per SM)
+#ifndef MP_TILE_SLOTS
+#define MP_TILE_SLOTS 3
+#endif
+constexpr int kTileSlots = MP_TILE_SLOTS;
+static_assert(kTileSlots == 3 || kTileSlots == 4, "ring of 3 or 4 planes");
+template <int kB>
+__host__ __device__ constexpr int tile_rows()
+{
+    return 2 * (kB / 32);
+}
+template <int kB>
+__host__ __device__ constexpr int tile_pos()
+{
+    return kTilePX * (tile_rows<kB>() + 2);
+}
+// dynamic shared memory of the tiled body: the ring (fields in two 16-byte halves, flow,
+// fluid-list and interface indices), the wrapped coordinates of the tile's columns and rows,
+// and each warp's lane map
+template <int kB>
+__host__ __device__ constexpr size_t tile_smem()
+{
+    return (size_t)kTileSlots * tile_pos<kB>() * (3 * sizeof(float4) + 2 * sizeof(int)) +
+           (size_t)(kTilePX + tile_rows<kB>() + 2) * sizeof(int) + (size_t)(kB / 32) * 64;
+}
+
+__device__ __forceinline__ int wrap_mod(int v, int n)
+{
+    const int r = v % n;
+    return r < 0 ? r + n : r;
+}
+
+__device__ __forceinline__ void cp_async_cg16(void* dst, const void* src)
+{
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"((uint32_t)__cvta_generic_to_shared(dst)),
+                 "l"(src)
+                 : "memory");
+}
+
+template <int FP, bool kCoherent, int kB>
+__device__ __forceinline__ void vblock_tiled(const DArgs& a, int vb, int in, double* part, bool acc_part,
+                                             double (*s_red)[kMaxSeries], const float* s_whf, const float* s_whe,
+                                             const float* s_pa, const float* s_pd, unsigned char* tsm)
+{
+    constexpr int kSC = 8 / FP;
+    constexpr int kOW4 = FP == 2 ? 2 : 4;
+    constexpr int kRows = tile_rows<kB>();
+    constexpr int kP = tile_pos<kB>();
+    constexpr int kPJ = (kP + kB - 1) / kB;  // positions per thread in a plane
+    using VC = FieldVec<float, 8>;
+    float4* sF0 = reinterpret_cast<float4*>(tsm);  // [slot][position]: fields 0..3 of the chunk
+    float4* sF1 = sF0 + kTileSlots * kP;            // fields 4..7
+    float4* sU = sF1 + kTileSlots * kP;             // flow vector
+    int* sK = reinterpret_cast<int*>(sU + kTileSlots * kP);  // fluid-list index, -1 if solid
+    int* sI = sK + kTileSlots * kP;                 // interface index, -1 off the interface
+    int* sX = sI + kTileSlots * kP;                 // lattice x of tile column 0..33
+    int* sY = sX + kTilePX;                         // lattice y of tile row 0..kRows+1
+    unsigned char* sMap = reinterpret_cast<unsigned char*>(sY + kRows + 2);  // [warp][64]
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const int tx = vb % a.ntx, t1 = vb / a.ntx, ty = t1 % a.nty, tzs = t1 / a.nty;
+    const float4 zero4 = make_float4(0.f, 0.f, 0.f, 0.f);
+    const int x0 = tx * kTileX, y0 = ty * kRows, z0 = tzs * a.tz;
+    const int z1 = min(z0 + a.tz, a.nz);
+    const int M = a.M, K = a.K;
+    const size_t NF = (size_t)a.NF, NI = (size_t)a.NI;
+    const float* Pin = a.P[in];
+    VC* Pout = reinterpret_cast<VC*>(a.P[1 - in]);
+    const VC* Ain = reinterpret_cast<const VC*>(a.A[in]);
+    VC* Aout = reinterpret_cast<VC*>(a.A[1 - in]);
+    __syncthreads();  // the previous virtual block is done with the shared tables
+    if (tid < kTilePX) sX[tid] = wrap_mod(x0 - 1 + tid, a.nx);
+    if (tid < kRows + 2) sY[tid] = wrap_mod(y0 - 1 + tid, a.ny);
+    for (int j = tid; j < kMaxSeries; j += kB)
+        for (int w = 0; w < kB / 32; ++w) s_red[w][j] = 0.0;
+    __syncthreads();
+
+    // lattice node of this thread's positions p = tid + kB j within a plane (without z)
+    int pxy[kPJ];
+#pragma unroll
+    for (int j = 0; j < kPJ; ++j) {
+        const int p = tid + kB * j;
+        const int ly = p / kTilePX, lx = p - ly * kTilePX;
+        pxy[j] = p < kP ? sY[ly] * a.nx + sX[lx] : 0;
+    }
+    // fluid and interface words of this thread's positions of plane z, and the positions' bit
+    // in them (fetched before their copies are issued, so that their latency overlaps work)
+    uint2 wf[kPJ], wi[kPJ];
+    int bj[kPJ];
+    auto fetch_words = [&](int z) {
+        const long long zoff = (long long)wrap_mod(z, a.nz) * a.ny * a.nx;
+#pragma unroll
+        for (int j = 0; j < kPJ; ++j) {
+            if (tid + kB * j < kP) {
+                const int n = (int)(zoff + pxy[j]);
+                bj[j] = n & 31;
+                wf[j] = __ldg(a.fw + (n >> 5));
+                wi[j] = __ldg(a.iw + (n >> 5));
+            }
+        }
+    };
+
+    const int cpn = a.SP / kSC;
+#pragma unroll 1
+    for (int ch = 0; ch < cpn; ++ch) {
+        const float* Pc = Pin + (size_t)ch * NF * 8;
+        // copies of plane z (z0 - 1 <= z <= z1) into its ring slot, from the fetched words
+        auto issue_plane = [&](int z) {
+            const int slot = (z - z0 + 1) % kTileSlots;
+#pragma unroll
+            for (int j = 0; j < kPJ; ++j) {
+                const int p = tid + kB * j;
+                if (p < kP) {
+                    const int b = bj[j];
+                    const uint32_t lt = (1u << b) - 1u;
+                    int kk = -1;
+                    if ((wf[j].x >> b) & 1u) {
+                        kk = (int)wf[j].y + __popc(wf[j].x & lt);
+                        const float* src = Pc + (size_t)kk * 8;
+                        cp_async_cg16(&sF0[slot * kP + p], src);
+                        cp_async_cg16(&sF1[slot * kP + p], src + 4);
+                        cp_async_cg16(&sU[slot * kP + p], a.uc + kk);
+                    } else {
+                        // a solid source: zero fields and flow, so that a closed link adds
+                        // p * 0 = 0 and the link loop needs no test
+                        sF0[slot * kP + p] = zero4;
+                        sF1[slot * kP + p] = zero4;
+                        sU[slot * kP + p] = zero4;
+                    }
+                    sK[slot * kP + p] = kk;
+                    sI[slot * kP + p] = ((wi[j].x >> b) & 1u) ? (int)wi[j].y + __popc(wi[j].x & lt) : -1;
+                }
+            }
+        };
+        __syncthreads();  // the previous chunk's march is done with the ring
+        fetch_words(z0 - 1);
+        issue_plane(z0 - 1);
+        asm volatile("cp.async.commit_group;" ::: "memory");
+        fetch_words(z0);
+        issue_plane(z0);
+        asm volatile("cp.async.commit_group;" ::: "memory");
+        fetch_words(z0 + 1);
+        issue_plane(z0 + 1);
+        asm volatile("cp.async.commit_group;" ::: "memory");
+        if (kTileSlots == 4 && z0 + 2 <= z1) fetch_words(z0 + 2);
+#pragma unroll 1
+        for (int z = z0; z < z1; ++z) {
+            if constexpr (kTileSlots == 4) {
+                // plane z + 2 into the slot of plane z - 2 (free since the last barrier); words
+                // of plane z + 3
+                if (z + 2 <= z1) issue_plane(z + 2);
+                asm volatile("cp.async.commit_group;" ::: "memory");
+                if (z + 3 <= z1) fetch_words(z + 3);
+                asm volatile("cp.async.wait_group 1;" ::: "memory");  // planes up to z + 1 have landed
+            } else {
+                if (z + 2 <= z1) fetch_words(z + 2);  // its copies follow this plane's work
+                asm volatile("cp.async.wait_group 0;" ::: "memory");
+            }
+            __syncthreads();
+            const int sc = (z - z0 + 1) % kTileSlots;
+            const int sm = (z - z0) % kTileSlots, sp = (z - z0 + 2) % kTileSlots;
+            // this warp's two rows: fluid nodes inside the lattice, packed onto the lanes
+            uint32_t bits[2];
+#pragma unroll
+            for (int r = 0; r < 2; ++r) {
+                const int ly = 1 + 2 * warp + r;
+                const bool fl = y0 + 2 * warp + r < a.ny && x0 + lane < a.nx &&
+                                sK[sc * kP + ly * kTilePX + 1 + lane] >= 0;
+                bits[r] = __ballot_sync(0xffffffffu, fl);
+                if (fl) sMap[warp * 64 + (r ? __popc(bits[0]) : 0) + __popc(bits[r] & ((1u << lane) - 1u))] =
+                    (unsigned char)((r << 5) | lane);
+            }
+            __syncwarp();
+            const int ntot = __popc(bits[0]) + __popc(bits[1]);
+            float zt[kSC * 3];
+#pragma unroll
+            for (int j = 0; j < kSC * 3; ++j) zt[j] = 0.f;
+            for (int j = lane; j < ntot; j += 32) {
+                const int e = sMap[warp * 64 + j];
+                const int pos = (1 + 2 * warp + (e >> 5)) * kTilePX + 1 + (e & 31);
+                const int kk = sK[sc * kP + pos];
+                const int ai = sI[sc * kP + pos];
+                // the node's record and adsorbed fields, requested before the link loop
+                const float4* o = reinterpret_cast<const float4*>(a.own) + (size_t)kk * kOW4;
+                const float4 o0 = __ldg(o);
+                float4 om[kOW4 - 1];
+#pragma unroll
+                for (int m = 0; m < kOW4 - 1; ++m) om[m] = m < M ? __ldg(o + 1 + m) : make_float4(0.f, 0.f, 0.f, 0.f);
+                const size_t ia = (size_t)ch * NI + (ai >= 0 ? ai : 0);
+                VC xa;
+                if (ai >= 0) xa = ld_field<kCoherent, 8>(Ain + ia);
+                float acc[8];
+#pragma unroll
+                for (int f = 0; f < 8; ++f) acc[f] = 0.f;
+#pragma unroll
+                for (int i = 1; i < kQ; ++i) {
+                    const int sl = cz(i) > 0 ? sm : (cz(i) < 0 ? sp : sc);
+                    const int q_at = sl * kP + pos - cx(i) - cy(i) * kTilePX;
+                    const float4 uf = sU[q_at];
+                    const float q = qlink(edot<float>(i, uf.x, uf.y, uf.z), uf.w);
+                    const float4 f0 = sF0[q_at], f1 = sF1[q_at];
+                    const float xs[8] = {f0.x, f0.y, f0.z, f0.w, f1.x, f1.y, f1.z, f1.w};
+#pragma unroll
+                    for (int qq = 0; qq < kSC; ++qq) {
+                        const int spc = ch * kSC + qq;
+                        const float pl = rn_fma(weight<float>(i), q, is_face(i) ? s_whf[spc] : s_whe[spc]);
+#pragma unroll
+                        for (int f = 0; f < FP; ++f) acc[qq * FP + f] = __fmaf_rn(pl, xs[qq * FP + f], acc[qq * FP + f]);
+                    }
+                }
+                const float4 r0 = sF0[sc * kP + pos], r1 = sF1[sc * kP + pos];
+                const float xr[8] = {r0.x, r0.y, r0.z, r0.w, r1.x, r1.y, r1.z, r1.w};
+                VC xn;
+#pragma unroll
+                for (int qq = 0; qq < kSC; ++qq) {
+                    const int spc = ch * kSC + qq;
+                    const float out =
+                        __fmaf_rn(o0.w, s_pa[spc], __fmaf_rn(o0.z, s_whe[spc], __fmaf_rn(o0.y, s_whf[spc], o0.x)));
+#pragma unroll
+                    for (int f = 0; f < FP; ++f) {
+                        const int j2 = qq * FP + f;
+                        xn.v[j2] = __fadd_rn(__fmaf_rn(-out, xr[j2], acc[j2]), xr[j2]);
+                    }
+                }
+                if (ai >= 0) {
+                    VC xan;
+#pragma unroll
+                    for (int qq = 0; qq < kSC; ++qq) {
+                        const int spc = ch * kSC + qq;
+                        const float pa = s_pa[spc], pd = s_pd[spc];
+#pragma unroll
+                        for (int f = 0; f < FP; ++f) {
+                            const int j2 = qq * FP + f;
+                            xn.v[j2] = __fmaf_rn(pd, xa.v[j2], xn.v[j2]);
+                            xan.v[j2] = __fmaf_rn(pa, xr[j2], __fmaf_rn(-pd, xa.v[j2], xa.v[j2]));
+                        }
+                    }
+                    st_field<8>(Aout + ia, xan);
+                }
+                st_field<8>(Pout + (size_t)ch * NF + kk, xn);
+#pragma unroll
+                for (int qq = 0; qq < kSC; ++qq) {
+                    const int spc = ch * kSC + qq;
+#pragma unroll
+                    for (int m = 0; m < 3; ++m) {
+                        if (m < M && 1 + m < FP) {
+                            const float us = __fmaf_rn(om[m].z, s_whe[spc], __fmaf_rn(om[m].y, s_whf[spc], om[m].x));
+                            zt[qq * 3 + m] += xn.v[qq * FP + ((1 + m) < FP ? 1 + m : 0)] * us;
+                        }
+                    }
+                }
+            }
+            // this plane's Z terms: warp sums (FP32), added to the warp's FP64 accumulators
+#pragma unroll
+            for (int qq = 0; qq < kSC; ++qq) {
+                const int spc = ch * kSC + qq;
+                if (spc < a.S) {
+#pragma unroll
+                    for (int m = 0; m < 3; ++m) {
+                        if (m < M) {
+                            const float w = warp_sum(zt[qq * 3 + m]);
+                            if (lane == 0) s_red[warp][spc * M + m] += (double)w;
+                        }
+                    }
+                }
+            }
+            __syncthreads();  // before the next copies reuse the slot of plane z - 1 (or z - 2)
+            if constexpr (kTileSlots == 3) {
+                if (z + 2 <= z1) issue_plane(z + 2);
+                asm volatile("cp.async.commit_group;" ::: "memory");
+            }
+        }
+        asm volatile("cp.async.wait_all;" ::: "memory");
+    }
+    block_store<kB>(s_red, K, part, acc_part);
+}
+
 // Several species: stage the per-species constants in shared memory (uniform across the
 // block) and run the body; block sums to part[0..K) (stored, or added when acc_part).
 template <int FP, bool kTable, bool kCoherent, int kB>
@@ -469,6 +811,20 @@ __device__ __forceinline__ void run_multi(const DArgs& a, int vb, int in, double
     __syncthreads();
     vblock_multi<FP, kTable, kCoherent, kB>(a, vb, in, part, acc_part, s_red, s_c, s_c + MP_MAX_SPECIES,
                                             s_c + 2 * MP_MAX_SPECIES, s_c + 3 * MP_MAX_SPECIES);
+}
+
+template <int FP, bool kCoherent, int kB>
+__device__ __forceinline__ void run_tiled(const DArgs& a, int vb, int in, double* part, bool acc_part,
+                                          double (*s_red)[kMaxSeries], float* s_c, unsigned char* tsm)
+{
+    for (int j = threadIdx.x; j < MP_MAX_SPECIES; j += kB) {
+        s_c[j] = a.whf[j];
+        s_c[MP_MAX_SPECIES + j] = a.whe[j];
+        s_c[2 * MP_MAX_SPECIES + j] = a.pa[j];
+        s_c[3 * MP_MAX_SPECIES + j] = a.pd[j];
+    }
+    vblock_tiled<FP, kCoherent, kB>(a, vb, in, part, acc_part, s_red, s_c, s_c + MP_MAX_SPECIES,
+                                            s_c + 2 * MP_MAX_SPECIES, s_c + 3 * MP_MAX_SPECIES, tsm);
 }
 
 __device__ __forceinline__ int ctx_of(const DLaunch& L, int v)
@@ -505,10 +861,13 @@ __device__ __forceinline__ double ctx_series_total(const double* part, int nvb, 
     return tot;
 }
 
-template <int FP, bool kSingle>
+template <int FP, bool kSingle, bool kTiled = false>
 constexpr int min_blocks_direct(int block)
 {
-    return kSingle ? MP_DIRECT_SINGLE_THREADS / block : (MP_DIRECT_MULTI_THREADS / block > 1 ? MP_DIRECT_MULTI_THREADS / block : 1);
+    // tiled: as many blocks as the shared-memory ring leaves room for (three of 128 threads)
+    return kTiled ? 3
+                  : (kSingle ? MP_DIRECT_SINGLE_THREADS / block
+                             : (MP_DIRECT_MULTI_THREADS / block > 1 ? MP_DIRECT_MULTI_THREADS / block : 1));
 }
 
 // Appends Z(t1), D(t1) = D(t1 - 1) + Z(t1) of every series of context a, t1 = t + 1, from
@@ -535,10 +894,11 @@ __device__ __forceinline__ void append_series(const DArgs& a, const double* part
 // step whose partials are not yet added), so no block waits for the others at the end; the
 // last step of a run is appended by k_direct_finish.
 // ---------------------------------------------------------------------------------------
-template <int FP, bool kSingle, bool kTable, int kB>
-__global__ void __launch_bounds__(kB, min_blocks_direct<FP, kSingle>(kB))
+template <int FP, bool kSingle, bool kTable, int kB, bool kTiled>
+__global__ void __launch_bounds__(kB, min_blocks_direct<FP, kSingle, kTiled>(kB))
     k_direct_step(const __grid_constant__ DLaunch L, int phase, int pending)
 {
+    extern __shared__ __align__(16) unsigned char tsm[];  // tiled variant's ring
     __shared__ double s_red[kB / 32][kMaxSeries];
     __shared__ float s_c[4 * MP_MAX_SPECIES];
     __shared__ double s_tmp[kB / 32];
@@ -556,6 +916,8 @@ __global__ void __launch_bounds__(kB, min_blocks_direct<FP, kSingle>(kB))
         float zacc[3] = {0.f, 0.f, 0.f};
         vblock_single<FP, kTable, false, kB>(a, vb, in, zacc);
         reduce_zacc<kB>(s_red, a.M, zacc, part, false);
+    } else if constexpr (kTiled) {
+        run_tiled<FP, false, kB>(a, vb, in, part, false, s_red, s_c, tsm);
     } else {
         run_multi<FP, kTable, false, kB>(a, vb, in, part, false, s_red, s_c);
     }
@@ -633,11 +995,12 @@ __device__ __forceinline__ bool grid_wait(unsigned int* count, unsigned int targ
 #endif
 constexpr bool kRoundRobin = MP_DIRECT_RR != 0;
 
-template <int FP, bool kSingle, bool kTable, int kB>
-__global__ void __launch_bounds__(kB, min_blocks_direct<FP, kSingle>(kB))
+template <int FP, bool kSingle, bool kTable, int kB, bool kTiled>
+__global__ void __launch_bounds__(kB, min_blocks_direct<FP, kSingle, kTiled>(kB))
     k_direct_persistent(const __grid_constant__ DLaunch L, int phase0, int nsteps, unsigned int* bar, int* err,
                         long long timeout_ns)
 {
+    extern __shared__ __align__(16) unsigned char tsm[];  // tiled variant's ring
     __shared__ double s_red[kB / 32][kMaxSeries];
     __shared__ double s_acc[kMaxSeries];
     __shared__ float s_c[4 * MP_MAX_SPECIES];
@@ -684,6 +1047,8 @@ __global__ void __launch_bounds__(kB, min_blocks_direct<FP, kSingle>(kB))
             const int in = (a.in0 + phase) & 1;
             if (kSingle || a.S == 1)
                 vblock_single<FP, kTable, true, kB>(a, v - L.vbofs[c], in, zacc);
+            else if constexpr (kTiled)
+                run_tiled<FP, true, kB>(a, v - L.vbofs[c], in, s_acc, true, s_red, s_c, tsm);
             else
                 run_multi<FP, kTable, true, kB>(a, v - L.vbofs[c], in, s_acc, true, s_red, s_c);
         }
@@ -705,6 +1070,22 @@ __global__ void k_grid_wait_selftest(int rounds, int unreachable, unsigned int* 
         const unsigned int target = (unsigned int)(r + 1) * gridDim.x + (unreachable ? 1u : 0u);
         if (!grid_wait(bar, target, err, timeout_ns)) return;
     }
+}
+
+// Fluid-list addressing of a several-species context (once, at mp_init): {bits, nodes before
+// the word} per 32-node word (of the fluid and of the interface), and the flow vectors in
+// list order.
+__global__ void k_fluid_words(const uint32_t* __restrict__ fluid, const int32_t* __restrict__ fbase, int W,
+                              uint2* __restrict__ fw)
+{
+    const int w = blockIdx.x * blockDim.x + threadIdx.x;
+    if (w < W) fw[w] = make_uint2(fluid[w], (uint32_t)fbase[w]);
+}
+__global__ void k_list_flow(const int32_t* __restrict__ flist, const Flow4<float>* __restrict__ u4, int NF,
+                            Flow4<float>* __restrict__ uc)
+{
+    const int k = blockIdx.x * blockDim.x + threadIdx.x;
+    if (k < NF) uc[k] = u4[flist[k]];
 }
 
 // ---------------------------------------------------------------------------------------
@@ -801,6 +1182,26 @@ __global__ void k_direct_tables(const int32_t* __restrict__ flist, const uint32_
 
 }  // namespace
 
+// Tiles of a several-species context for the tiled variant: 32 x 8 columns, planes per tile
+// chosen so that the tiles fill the device about eight times over (at least two planes).
+void set_tiles(DArgs& a, int sms)
+{
+    a.ntx = (a.nx + kTileX - 1) / kTileX;
+    a.nty = (a.ny + tile_rows<128>() - 1) / tile_rows<128>();
+    const long long cols = (long long)a.ntx * a.nty;
+    const long long want = 8LL * 3 * std::max(sms, 1);
+    long long tz = (cols * a.nz + want - 1) / want;
+    tz = std::max(2LL, std::min<long long>(tz, a.nz));
+    a.tz = (int)tz;
+}
+int tiles_of(const DArgs& a) { return a.ntx * a.nty * ((a.nz + a.tz - 1) / a.tz); }
+// virtual blocks of the untiled variants at the smallest block (128), or tiles
+size_t part_rows(const DArgs& a)
+{
+    const size_t rows = (size_t)((a.NF + 127) / 128);
+    return a.S > 1 ? std::max(rows, (size_t)tiles_of(a)) : rows;
+}
+
 // ---------------------------------------------------------------------------------------
 // Launch state over a set of contexts
 // ---------------------------------------------------------------------------------------
@@ -813,6 +1214,7 @@ struct DirectState {
     int block = 256;
     bool table = true;
     bool persistent = false;
+    bool tiled = false;  // several-species contexts by tiles (block 128)
     int phase = 0;
     DArgs* d_args = nullptr;
     std::vector<DArgs> h_args;
@@ -827,11 +1229,26 @@ struct DirectState {
 
 namespace {
 
-template <int FP, bool kSingle, bool kTable, int kB>
+template <bool kTiled, int kB>
+constexpr size_t dyn_smem()
+{
+    return kTiled ? tile_smem<kB>() : 0;
+}
+
+template <int FP, bool kSingle, bool kTable, int kB, bool kTiled>
 cudaError_t launch_step_t(DirectState* d, int pending)
 {
-    return launch_pdl(k_direct_step<FP, kSingle, kTable, kB>, dim3(d->L.vbofs[d->L.n]), dim3(kB), d->stream, d->L,
-                      d->phase, pending);
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(d->L.vbofs[d->L.n]);
+    cfg.blockDim = dim3(kB);
+    cfg.dynamicSmemBytes = dyn_smem<kTiled, kB>();
+    cfg.stream = d->stream;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    attr[0].val.programmaticStreamSerializationAllowed = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    return cudaLaunchKernelEx(&cfg, k_direct_step<FP, kSingle, kTable, kB, kTiled>, d->L, d->phase, pending);
 }
 
 // appends the series of the last step (parity `phase`) of a run of one-step launches
@@ -840,7 +1257,7 @@ cudaError_t launch_finish(DirectState* d, int phase)
     return launch_pdl(k_direct_finish<256>, dim3(d->L.n), dim3(256), d->stream, d->L, phase);
 }
 
-template <int FP, bool kSingle, bool kTable, int kB>
+template <int FP, bool kSingle, bool kTable, int kB, bool kTiled>
 cudaError_t launch_persistent_t(DirectState* d, int nsteps)
 {
     cudaError_t e = cudaMemsetAsync(d->bar, 0, sizeof(unsigned int), d->stream);
@@ -848,34 +1265,48 @@ cudaError_t launch_persistent_t(DirectState* d, int nsteps)
     cudaLaunchConfig_t cfg = {};
     cfg.gridDim = dim3(d->pgrid);
     cfg.blockDim = dim3(kB);
+    cfg.dynamicSmemBytes = dyn_smem<kTiled, kB>();
     cfg.stream = d->stream;
     cudaLaunchAttribute attr[1];
     attr[0].id = cudaLaunchAttributeCooperative;
     attr[0].val.cooperative = 1;
     cfg.attrs = attr;
     cfg.numAttrs = 1;
-    return cudaLaunchKernelEx(&cfg, k_direct_persistent<FP, kSingle, kTable, kB>, d->L, d->phase, nsteps, d->bar,
-                              d->err, kWaitNs);
+    return cudaLaunchKernelEx(&cfg, k_direct_persistent<FP, kSingle, kTable, kB, kTiled>, d->L, d->phase, nsteps,
+                              d->bar, d->err, kWaitNs);
 }
 
-template <int FP, bool kSingle, bool kTable, int kB>
+// allows the tiled instances their dynamic shared memory; the persistent grid's blocks per SM
+template <int FP, bool kSingle, bool kTable, int kB, bool kTiled>
 int occupancy_t(int* blocks_per_sm)
 {
-    return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, k_direct_persistent<FP, kSingle, kTable, kB>,
-                                                         kB, 0) == cudaSuccess
+    if (kTiled) {
+        const int bytes = (int)dyn_smem<kTiled, kB>();
+        if (cudaFuncSetAttribute(k_direct_step<FP, kSingle, kTable, kB, kTiled>,
+                                 cudaFuncAttributeMaxDynamicSharedMemorySize, bytes) != cudaSuccess ||
+            cudaFuncSetAttribute(k_direct_persistent<FP, kSingle, kTable, kB, kTiled>,
+                                 cudaFuncAttributeMaxDynamicSharedMemorySize, bytes) != cudaSuccess)
+            return MP_ECUDA;
+    }
+    return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm,
+                                                         k_direct_persistent<FP, kSingle, kTable, kB, kTiled>, kB,
+                                                         dyn_smem<kTiled, kB>()) == cudaSuccess
                ? MP_OK
                : MP_ECUDA;
 }
 
 // dispatch over the compile-time variants: fields per record, one or several species, table or
-// recomputed link terms, block size
+// recomputed link terms, block size, tiled (several species, block 128)
 template <typename Fn>
 auto dispatch(const DirectState* d, Fn&& fn)
 {
     auto by_block = [&](auto fp, auto single, auto table) {
-        if (d->block == 128) return fn(fp, single, table, std::integral_constant<int, 128>{});
-        if (d->block == 512) return fn(fp, single, table, std::integral_constant<int, 512>{});
-        return fn(fp, single, table, std::integral_constant<int, 256>{});
+        if constexpr (!decltype(single)::value && !decltype(table)::value) {
+            if (d->tiled) return fn(fp, single, table, std::integral_constant<int, 128>{}, std::true_type{});
+        }
+        if (d->block == 128) return fn(fp, single, table, std::integral_constant<int, 128>{}, std::false_type{});
+        if (d->block == 512) return fn(fp, single, table, std::integral_constant<int, 512>{}, std::false_type{});
+        return fn(fp, single, table, std::integral_constant<int, 256>{}, std::false_type{});
     };
     auto by_table = [&](auto fp, auto single) {
         if (d->table) return by_block(fp, single, std::true_type{});
@@ -891,26 +1322,26 @@ auto dispatch(const DirectState* d, Fn&& fn)
 
 cudaError_t launch_step(DirectState* d, int pending)
 {
-    return dispatch(d, [&](auto fp, auto single, auto table, auto kb) {
+    return dispatch(d, [&](auto fp, auto single, auto table, auto kb, auto tiled) {
         return launch_step_t<decltype(fp)::value, decltype(single)::value, decltype(table)::value,
-                             decltype(kb)::value>(d, pending);
+                             decltype(kb)::value, decltype(tiled)::value>(d, pending);
     });
 }
 
 cudaError_t launch_persistent(DirectState* d, int nsteps)
 {
-    return dispatch(d, [&](auto fp, auto single, auto table, auto kb) {
+    return dispatch(d, [&](auto fp, auto single, auto table, auto kb, auto tiled) {
         return launch_persistent_t<decltype(fp)::value, decltype(single)::value, decltype(table)::value,
-                                   decltype(kb)::value>(d, nsteps);
+                                   decltype(kb)::value, decltype(tiled)::value>(d, nsteps);
     });
 }
 
 int persistent_grid(DirectState* d)
 {
     int per_sm = 0;
-    int rc = dispatch(d, [&](auto fp, auto single, auto table, auto kb) {
-        return occupancy_t<decltype(fp)::value, decltype(single)::value, decltype(table)::value, decltype(kb)::value>(
-            &per_sm);
+    int rc = dispatch(d, [&](auto fp, auto single, auto table, auto kb, auto tiled) {
+        return occupancy_t<decltype(fp)::value, decltype(single)::value, decltype(table)::value, decltype(kb)::value,
+                           decltype(tiled)::value>(&per_sm);
     });
     if (rc != MP_OK) return rc;
     int dev = 0, sms = 0;
@@ -939,15 +1370,15 @@ int upload_args(DirectState* d)
     d->L.vbofs[0] = 0;
     for (int c = 0; c < n; ++c) {
         DArgs& a = d->h_args[c];
-        a.nvb = (int)((d->ctx[c]->geo.n_fluid + d->block - 1) / d->block);
+        a.nvb = d->tiled && a.S > 1 ? tiles_of(a) : (int)((d->ctx[c]->geo.n_fluid + d->block - 1) / d->block);
         d->L.vbofs[c + 1] = d->L.vbofs[c] + a.nvb;
     }
-    // partials: [2][nvb][K] per context, sized for the smallest block (128)
+    // partials: [2][nvb][K] per context, sized for the most virtual blocks of any variant
     size_t off = 0;
     for (int c = 0; c < n; ++c) {
         DArgs& a = d->h_args[c];
         a.part = d->part + off;
-        off += 2 * (size_t)((d->ctx[c]->geo.n_fluid + 127) / 128) * a.K;
+        off += 2 * part_rows(a) * a.K;
     }
     MP_CUDA(cudaMemcpyAsync(d->d_args, d->h_args.data(), sizeof(DArgs) * n, cudaMemcpyHostToDevice, d->stream));
     MP_CUDA(cudaStreamSynchronize(d->stream));
@@ -962,7 +1393,8 @@ void set_variant_name(DirectState* d)
 {
     // a persistent variant that found no room for its grid runs one launch per step
     d->variant = std::string(d->persistent && d->pgrid > 0 ? "persistent" : "per-step") +
-                 (d->table ? ",table" : ",recompute") + ",block=" + std::to_string(d->block);
+                 (d->table ? ",table" : ",recompute") +
+                 (d->tiled ? ",tiled,block=128" : ",block=" + std::to_string(d->block));
 }
 
 // advance the bookkeeping of every context by n steps
@@ -1053,11 +1485,14 @@ int autotune(DirectState* d, int steps)
     struct Cand {
         bool table, persistent;
         int block;
+        bool tiled;
     };
     std::vector<Cand> cands;
     for (int tb = 1; tb >= 0; --tb)
-        for (int ps = 0; ps < 2; ++ps)
-            for (int blk : {128, 256, 512}) cands.push_back({tb != 0, ps != 0, blk});
+        for (int ps = 0; ps < 2; ++ps) {
+            for (int blk : {128, 256, 512}) cands.push_back({tb != 0, ps != 0, blk, false});
+            if (!d->single && tb == 0) cands.push_back({false, ps != 0, 128, true});
+        }
     const size_t n = d->ctx.size();
     std::vector<void*> bP(n, nullptr), bA(n, nullptr);
     std::vector<size_t> nP(n), nA(n);
@@ -1066,7 +1501,7 @@ int autotune(DirectState* d, int steps)
     for (size_t c = 0; c < n && rc == MP_OK; ++c) {
         mp_ctx* x = d->ctx[c];
         const size_t NI = (size_t)(x->geo.n_iface > 0 ? x->geo.n_iface : 1);
-        nP[c] = (size_t)x->SP * x->geo.N * x->FP * sizeof(float);
+        nP[c] = (size_t)x->SP * (x->compact ? (size_t)x->geo.n_fluid : (size_t)x->geo.N) * x->FP * sizeof(float);
         nA[c] = (size_t)x->SP * NI * x->FP * sizeof(float);
         t0[c] = x->t;
         if (cudaMalloc(&bP[c], nP[c]) != cudaSuccess || cudaMalloc(&bA[c], nA[c]) != cudaSuccess) {
@@ -1087,12 +1522,13 @@ int autotune(DirectState* d, int steps)
             rc = cuda_fail(cudaGetLastError(), "autotune: backup");
     }
     float best_ms = 1e30f;
-    Cand best{d->table, d->persistent, d->block};
+    Cand best{d->table, d->persistent, d->block, d->tiled};
     for (const Cand& cd : cands) {
         if (rc != MP_OK) break;
         d->table = cd.table;
         d->persistent = cd.persistent;
         d->block = cd.block;
+        d->tiled = cd.tiled;
         rc = upload_args(d);
         if (rc != MP_OK) break;
         if (d->persistent && d->pgrid == 0) continue;
@@ -1128,6 +1564,7 @@ int autotune(DirectState* d, int steps)
     d->table = best.table;
     d->persistent = best.persistent;
     d->block = best.block;
+    d->tiled = best.tiled;
     const int rc2 = upload_args(d);
     set_variant_name(d);
     return rc != MP_OK ? rc : rc2;
@@ -1157,6 +1594,9 @@ DArgs make_dargs(mp_ctx* c)
     a.tab = c->dtab->tab;
     a.own = c->dtab->own;
     a.u4 = (const Flow4<float>*)c->u4;
+    a.fw = c->dtab->fw;
+    a.iw = c->dtab->iw;
+    a.uc = c->dtab->uc;
     for (int b = 0; b < 2; ++b) {
         a.P[b] = (float*)c->P[b];
         a.A[b] = (float*)c->A[b];
@@ -1196,10 +1636,19 @@ int direct_state_create(mp_ctx* const* ctxs, int n, cudaStream_t stream, int tun
     d->table = !(variant & MP_VARIANT_RECOMPUTE);
     d->persistent = (variant & MP_VARIANT_PERSISTENT) != 0;
     d->block = (variant & MP_VARIANT_BLOCK128) ? 128 : ((variant & MP_VARIANT_BLOCK512) ? 512 : 256);
+    d->tiled = (variant & MP_VARIANT_TILED) != 0 && !d->single;
+    if (d->tiled) d->table = false;  // the tiled body recomputes the link terms
+    int dev = 0, sms = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) {
+        delete d;
+        set_error("direct scheme: device query failed");
+        return MP_ECUDA;
+    }
     size_t part_elems = 0;
     for (mp_ctx* c : d->ctx) {
         d->h_args.push_back(make_dargs(c));
-        part_elems += 2 * (size_t)((c->geo.n_fluid + 127) / 128) * (size_t)(c->S * c->M);
+        set_tiles(d->h_args.back(), sms);
+        part_elems += 2 * part_rows(d->h_args.back()) * (size_t)(c->S * c->M);
     }
     cudaError_t e = cudaMalloc(&d->d_args, sizeof(DArgs) * n);
     if (e == cudaSuccess) e = cudaMalloc(&d->part, sizeof(double) * std::max<size_t>(part_elems, 1));
@@ -1309,6 +1758,18 @@ int direct_setup(mp_ctx* c, int tune, int variant)
         c->geo.ny, c->geo.nz, make_div((unsigned)c->geo.nx), make_div((unsigned)(c->geo.nx * c->geo.ny)),
         c->S == 1 ? 1 : 0, c->M, c->dir[0], c->dir[1], c->dir[2], whf, whe, (float)c->ka[0], t->aidx, t->tab, t->own);
     MP_CUDA(cudaGetLastError());
+    if (c->compact) {
+        MP_CUDA(cudaMalloc(&t->fw, sizeof(uint2) * (size_t)c->geo.W));
+        MP_CUDA(cudaMalloc(&t->iw, sizeof(uint2) * (size_t)c->geo.W));
+        MP_CUDA(cudaMalloc(&t->uc, sizeof(Flow4<float>) * NF));
+        k_fluid_words<<<(unsigned)((c->geo.W + 255) / 256), 256, 0, c->stream>>>(c->geo.fluid, c->geo.fbase, c->geo.W,
+                                                                                   t->fw);
+        k_fluid_words<<<(unsigned)((c->geo.W + 255) / 256), 256, 0, c->stream>>>(c->geo.iface, c->geo.ibase, c->geo.W,
+                                                                                   t->iw);
+        k_list_flow<<<(unsigned)((NF + 255) / 256), 256, 0, c->stream>>>(t->flist, (const Flow4<float>*)c->u4, (int)NF,
+                                                                          t->uc);
+        MP_CUDA(cudaGetLastError());
+    }
     mp_ctx* one[1] = {c};
     return direct_state_create(one, 1, c->stream, tune, variant, &c->dstate);
 }
@@ -1327,6 +1788,9 @@ void direct_free(mp_ctx* c)
         cudaFree(c->dtab->aidx);
         cudaFree(c->dtab->tab);
         cudaFree(c->dtab->own);
+        cudaFree(c->dtab->fw);
+        cudaFree(c->dtab->iw);
+        cudaFree(c->dtab->uc);
         delete c->dtab;
     }
     c->dtab = nullptr;

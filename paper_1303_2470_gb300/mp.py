@@ -43,6 +43,7 @@ MP_VARIANT_RECOMPUTE = 1
 MP_VARIANT_PERSISTENT = 2
 MP_VARIANT_BLOCK128 = 4
 MP_VARIANT_BLOCK512 = 8
+MP_VARIANT_TILED = 16
 
 _c_int, _c_i64, _c_dbl, _c_vp = ctypes.c_int, ctypes.c_int64, ctypes.c_double, ctypes.c_void_p
 

@@ -40,7 +40,8 @@ def _d_err(Dg, Do):
 
 def _variants(mp):
     R, P, B1, B5 = mp.MP_VARIANT_RECOMPUTE, mp.MP_VARIANT_PERSISTENT, mp.MP_VARIANT_BLOCK128, mp.MP_VARIANT_BLOCK512
-    return [0, R, P, R | P, B1, P | B5, R | P | B1]
+    T = mp.MP_VARIANT_TILED
+    return [0, R, P, R | P, B1, P | B5, R | P | B1, T, T | R, T | P, T | R | P]
 
 
 @pytest.mark.parametrize("species", [1, 3, 9])
@@ -48,7 +49,8 @@ def _variants(mp):
 def test_direct_matches_oracle_every_variant(mp, species, dirs):
     """Ragged 21x17x13 random medium with flow and sorption, 300 steps: every variant's Z, D
     and fields match the oracle; all variants give identical fields, and series equal up to
-    the order of their FP64 partial sums."""
+    the order of their FP64 partial sums (tiled variants with several species: up to the
+    grouping of their FP32 warp sums, which covers other nodes)."""
     solid, _ = media.random_spheres((13, 17, 21), 2.5, 0.6, seed=4)
     u = media.drift_flow(solid, 0.01, 0.02, seed=9).astype(np.float32)
     Db, ka, kd = media.species(species, seed=40 + species, D_b=(0.03, 0.1), k=(1e-3, 5e-2))
@@ -83,7 +85,8 @@ def test_direct_matches_oracle_every_variant(mp, species, dirs):
                 if kind == "field":
                     assert np.array_equal(a, b), var
                 else:
-                    assert np.max(np.abs(a - b)) <= 1e-12 * np.abs(b).max(), var
+                    tol = 1e-6 if (var & mp.MP_VARIANT_TILED and species > 1) else 1e-12
+                    assert np.max(np.abs(a - b)) <= tol * np.abs(b).max(), var
         ctx.close()
 
 
