@@ -1,6 +1,7 @@
 // lattice.cuh -- small device helpers shared by the moment-propagation kernels of libmp
 // (not part of the C ABI): the packed flow vector, exact division by a lattice extent,
-// periodic neighbour offsets, vector records of the propagated fields and warp sums.
+// periodic neighbour offsets, fluid-list indices of link sources, vector records of the
+// propagated fields and warp sums.
 #pragma once
 
 #include <cuda_runtime.h>
@@ -95,6 +96,45 @@ __device__ __forceinline__ int src_of(const Nbr& b, int i)
 {
     return b.n + (cx(i) > 0 ? b.oxm : (cx(i) < 0 ? b.oxp : 0)) + (cy(i) > 0 ? b.oym : (cy(i) < 0 ? b.oyp : 0)) +
            (cz(i) > 0 ? b.ozm : (cz(i) < 0 ? b.ozp : 0));
+}
+
+// Index of fluid node s in the sorted fluid list: fluid nodes before its 32-node word plus
+// those below it within the word.
+__device__ __forceinline__ int fluid_index(const uint2* __restrict__ fw, int s)
+{
+    const uint2 w = __ldg(fw + (s >> 5));
+    return (int)w.y + __popc(w.x & ((1u << (s & 31)) - 1u));
+}
+
+// The sources r - c_i lie in nine lattice rows (fixed y and z) around r: r's own row
+// (links 1, 2) and eight others, row j holding the source of link row_centre(j) (c_x = 0)
+// and, for four of them, the sources at x - 1 (link with c_x = +1) and x + 1 (c_x = -1).
+// Fluid nodes of a row are consecutive in the fluid list, so one located centre per row
+// gives the indices of its x - 1 and x + 1 neighbours.
+__host__ __device__ constexpr int row_of(int i)
+{
+    constexpr int t[kQ] = {-1, -1, -1, 0, 1, 0, 1, 1, 0, 2, 2, 2, 4, 5, 3, 3, 3, 6, 7};
+    return t[i];
+}
+__host__ __device__ constexpr int row_centre(int j)
+{
+    constexpr int t[8] = {3, 4, 9, 14, 12, 13, 17, 18};
+    return t[j];
+}
+
+// Fluid-list index of the source r - c_i of an open link i of fluid node r (index k, its
+// periodic neighbourhood b, open-link mask `mask`, C[j] = fluid_index of row j's centre,
+// xlo / xhi: x - 1 / x + 1 lie in r's row without wrapping): the row's centre, or its x -/+ 1
+// neighbour (own row: k -/+ 1); located directly where x - 1 or x + 1 wraps around.
+__device__ __forceinline__ int source_index(int i, int k, const int (&C)[8], uint32_t mask, bool xlo, bool xhi,
+                                            const Nbr& b, const uint2* __restrict__ fw)
+{
+    const int row = row_of(i);
+    const int base = row < 0 ? k : C[row < 0 ? 0 : row];
+    if (cx(i) == 0) return base;
+    if (cx(i) > 0) return xlo ? base - 1 : fluid_index(fw, src_of(b, i));
+    return xhi ? base + (row < 0 ? 1 : (int)((mask >> (row_centre(row < 0 ? 0 : row) - 1)) & 1u))
+               : fluid_index(fw, src_of(b, i));
 }
 
 template <typename T>

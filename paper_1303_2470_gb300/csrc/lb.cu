@@ -30,10 +30,11 @@ using namespace mp;
 namespace {
 
 constexpr int kLbThreads = 256;
-// 8 resident blocks per SM (32 registers a thread): the LB step is bound by instruction issue
-// and measured faster at full occupancy than with a larger register budget
+// 5 resident blocks per SM (48 registers a thread): with sources located by row (eight
+// prefix + popcount lookups a node) the step keeps its 19 gathers and the row centres in
+// registers; measured at 8, 6, 5 and 4 blocks (32 registers spill), 5 is fastest
 #ifndef MP_LB_MIN_BLOCKS
-#define MP_LB_MIN_BLOCKS 8
+#define MP_LB_MIN_BLOCKS 5
 #endif
 
 struct LbArgs {
@@ -42,6 +43,8 @@ struct LbArgs {
     const uint32_t* fluid;
     const int32_t* fbase;    // fluid nodes before each 32-node word
     const int32_t* flist;    // lattice node of fluid index k
+    const uint32_t* omask;   // open-link mask of fluid index k (bit i-1: r - c_i is fluid)
+    const uint2* fw;         // {fluid bits, fluid nodes before the word} per 32-node word
     const uint32_t* forced;  // the force acts on these nodes (the largest fluid cluster)
     float Fx, Fy, Fz;
     float inv_tau;
@@ -68,21 +71,22 @@ __global__ void __launch_bounds__(kLbThreads, MP_LB_MIN_BLOCKS)
     double res = 0.0;
     if (k < a.NF) {
         const int n = __ldg(a.flist + k);
+        const uint32_t mask = __ldg(a.omask + k);
         const Nbr b = nbrs_of(a.nx, a.ny, a.nz, a.dx, a.dxy, n);
+        // fluid-list index of each source row's centre; sources in a row are consecutive
+        int C[8];
+#pragma unroll
+        for (int j = 0; j < 8; ++j) C[j] = fluid_index(a.fw, src_of(b, row_centre(j)));
+        const bool xlo = b.oxm == -1, xhi = b.oxp == 1;
         float f[kQ];
 #pragma unroll
         for (int i = 0; i < kQ; ++i) {
             if (i == 0) {
                 f[0] = g[k];
+            } else if ((mask >> (i - 1)) & 1u) {
+                f[i] = g[(size_t)i * NF + source_index(i, k, C, mask, xlo, xhi, b, a.fw)];
             } else {
-                const int s = src_of(b, i);
-                const uint32_t bits = __ldg(a.fluid + (s >> 5));
-                if ((bits >> (s & 31)) & 1u) {
-                    const int ks = __ldg(a.fbase + (s >> 5)) + __popc(bits & ((1u << (s & 31)) - 1u));
-                    f[i] = g[(size_t)i * NF + ks];
-                } else {
-                    f[i] = g[(size_t)opposite(i) * NF + k];  // halfway bounce-back
-                }
+                f[i] = g[(size_t)opposite(i) * NF + k];  // halfway bounce-back
             }
         }
         float drho = 0.f, mx = 0.f, my = 0.f, mz = 0.f;
@@ -187,6 +191,24 @@ __global__ void k_lb_init(const LbArgs a, const float* __restrict__ u0, const fl
 
 }  // namespace
 
+// Per lb_steady call: the open-link mask of every fluid node and the {fluid bits, prefix}
+// words that locate link sources in the fluid list.
+__global__ void k_lb_prep(const LbArgs a, int W, uint32_t* __restrict__ omask, uint2* __restrict__ fw)
+{
+    const int t = blockIdx.x * blockDim.x + threadIdx.x;
+    if (t < W) fw[t] = make_uint2(a.fluid[t], (uint32_t)a.fbase[t]);
+    if (t < a.NF) {
+        const Nbr b = nbrs_of(a.nx, a.ny, a.nz, a.dx, a.dxy, a.flist[t]);
+        uint32_t m = 0;
+#pragma unroll
+        for (int i = 1; i < kQ; ++i) {
+            const int s = src_of(b, i);
+            if ((a.fluid[s >> 5] >> (s & 31)) & 1u) m |= 1u << (i - 1);
+        }
+        omask[t] = m;
+    }
+}
+
 extern "C" int lb_steady(const mp_geometry* geom, const double force[3], double tau, double tol, int64_t max_steps,
                          int64_t check_every, const float* u_init, const float* rho_init, float* u_out,
                          float* rho_out, int64_t* steps_out, double* residual_out, void* stream_ptr)
@@ -211,8 +233,12 @@ extern "C" int lb_steady(const mp_geometry* geom, const double force[3], double 
     const size_t N = (size_t)G.N;
     const size_t NF = (size_t)(G.n_fluid > 0 ? G.n_fluid : 1);
     float *g0 = nullptr, *g1 = nullptr, *uprev = nullptr;
+    uint32_t* omask = nullptr;
+    uint2* fw = nullptr;
     unsigned long long* res_d = nullptr;
     cudaError_t e = cudaMallocAsync((void**)&g0, sizeof(float) * kQ * NF, s);
+    if (e == cudaSuccess) e = cudaMallocAsync((void**)&omask, sizeof(uint32_t) * NF, s);
+    if (e == cudaSuccess) e = cudaMallocAsync((void**)&fw, sizeof(uint2) * (size_t)(G.W > 0 ? G.W : 1), s);
     if (e == cudaSuccess) e = cudaMallocAsync((void**)&g1, sizeof(float) * kQ * NF, s);
     if (e == cudaSuccess) e = cudaMallocAsync((void**)&uprev, sizeof(float) * 3 * NF, s);
     if (e == cudaSuccess) e = cudaMallocAsync((void**)&res_d, sizeof(unsigned long long), s);
@@ -223,6 +249,8 @@ extern "C" int lb_steady(const mp_geometry* geom, const double force[3], double 
         if (g0) cudaFreeAsync(g0, s);
         if (g1) cudaFreeAsync(g1, s);
         if (uprev) cudaFreeAsync(uprev, s);
+        if (omask) cudaFreeAsync(omask, s);
+        if (fw) cudaFreeAsync(fw, s);
         if (res_d) cudaFreeAsync(res_d, s);
         free_geometry(&G, s, true);
         cudaStreamSynchronize(s);
@@ -243,6 +271,8 @@ extern "C" int lb_steady(const mp_geometry* geom, const double force[3], double 
     a.fluid = G.fluid;
     a.fbase = G.fbase;
     a.flist = G.flist;
+    a.omask = omask;
+    a.fw = fw;
     a.forced = G.cluster;
     a.Fx = (float)force[0];
     a.Fy = (float)force[1];
@@ -252,6 +282,8 @@ extern "C" int lb_steady(const mp_geometry* geom, const double force[3], double 
     // one thread per fluid node (at least one block, so that a medium without fluid still
     // runs its checks: its residual is 0)
     const int blocks = (int)((NF + kLbThreads - 1) / kLbThreads);
+    const size_t prep = std::max<size_t>(NF, (size_t)G.W);
+    k_lb_prep<<<(unsigned)((prep + 255) / 256), 256, 0, s>>>(a, G.W, omask, fw);
     k_lb_init<<<blocks, kLbThreads, 0, s>>>(a, u_init, rho_init, g0, uprev);
     e = cudaGetLastError();
     int64_t t = 0;

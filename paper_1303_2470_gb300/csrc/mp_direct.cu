@@ -318,30 +318,6 @@ __device__ __forceinline__ void reduce_zacc(double (*s_red)[kMaxSeries], int M, 
     block_store<kB>(s_red, M, out, accumulate);
 }
 
-// Index of fluid node s in the sorted fluid list: fluid nodes before its 32-node word plus
-// those below it within the word.
-__device__ __forceinline__ int fluid_index(const uint2* __restrict__ fw, int s)
-{
-    const uint2 w = __ldg(fw + (s >> 5));
-    return (int)w.y + __popc(w.x & ((1u << (s & 31)) - 1u));
-}
-
-// The sources r - c_i lie in nine lattice rows (fixed y and z) around r: r's own row
-// (links 1, 2) and eight others, row j holding the source of link row_centre(j) (c_x = 0)
-// and, for four of them, the sources at x - 1 (link with c_x = +1) and x + 1 (c_x = -1).
-// Fluid nodes of a row are consecutive in the fluid list, so one located centre per row
-// gives the indices of its x - 1 and x + 1 neighbours.
-__host__ __device__ constexpr int row_of(int i)
-{
-    constexpr int t[kQ] = {-1, -1, -1, 0, 1, 0, 1, 1, 0, 2, 2, 2, 4, 5, 3, 3, 3, 6, 7};
-    return t[i];
-}
-__host__ __device__ constexpr int row_centre(int j)
-{
-    constexpr int t[8] = {3, 4, 9, 14, 12, 13, 17, 18};
-    return t[j];
-}
-
 // Several species: fields chunk-major over the fluid list, [chunk][k][8 floats] with 8/FP
 // species per chunk (k = index in the sorted fluid list = work item). The link loop is
 // outermost within a pass of up to two chunks: q_i is read (or recomputed) once per link and
@@ -395,18 +371,7 @@ __device__ __forceinline__ void vblock_multi(const DArgs& a, int vb, int in, dou
 #pragma unroll
             for (int i = 1; i < kQ; ++i) {
                 if (!((mask >> (i - 1)) & 1u)) continue;
-                const int row = row_of(i);
-                // fluid-list index of the source: the row's centre, or its x -/+ 1 neighbour
-                // (own row: k -/+ 1); located directly where x - 1 or x + 1 wraps around
-                const int base = row < 0 ? k : C[row < 0 ? 0 : row];
-                int s;
-                if (cx(i) == 0)
-                    s = base;
-                else if (cx(i) > 0)
-                    s = xlo ? base - 1 : fluid_index(a.fw, src_of(b, i));
-                else
-                    s = xhi ? base + (row < 0 ? 1 : (int)((mask >> (row_centre(row < 0 ? 0 : row) - 1)) & 1u))
-                            : fluid_index(a.fw, src_of(b, i));
+                const int s = source_index(i, k, C, mask, xlo, xhi, b, a.fw);
                 float q;
                 if constexpr (kTable) {
                     q = ld_stream(a.tab + tab_at(k, i));
