@@ -385,69 +385,60 @@ def run_batched(args):
     return 0
 
 
-def run_surrogate(args):
-    """LB warm start from the trained surrogate against the cold start (both to residual
-    1e-7, checked every 10 steps, at the force giving the benchmark's mean interstitial
-    velocity 0.01): unseen 64^3 media, the benchmark's 128^3 medium and unseen 256^3 media. Reports steps and wall time (the warm time includes the network's inference),
-    the estimate's error, the distance between the two converged flows and, on the benchmark
-    medium, the largest relative difference of D(t) over 2000 MP steps run on either flow."""
+def warm_start_case(mp, surrogate, model, media, label, n, R, phi, seed, check=10, force=None, d_steps=0):
+    """One medium solved by lb_steady to residual 1e-7 from rest and from the surrogate's warm
+    start: steps, wall times (the warm time includes the network's inference), the estimate's
+    error and the distance between the two converged flows; with d_steps > 0 also the largest
+    relative difference of D(t) of the benchmark's tracer over d_steps MP steps on either flow.
+    force: the body force; None calibrates it (untimed) to the benchmark's mean velocity 0.01."""
     import torch
-    from paper_1303_2470_gb300 import build, media
-    build.build()
-    from paper_1303_2470_gb300 import mp, surrogate
-    model, meta = surrogate.load()
-    rng = np.random.default_rng(77)
-    cases = [("unseen 64^3", 64, int(rng.integers(4, 9)), float(rng.uniform(0.3, 0.6)), 90_001 + i) for i in range(8)]
-    cases += [("benchmark medium 128^3", 128, WORKLOAD["radius"], WORKLOAD["porosity"], WORKLOAD["seed"])]
-    cases += [("unseen 256^3", 256, 6, 0.40, 90_101), ("unseen 256^3", 256, 5, 0.50, 90_102)]
-    out = []
-    check = 10
-    for label, n, R, phi, seed in cases:
-        solid, _ = media.random_spheres((n, n, n), R, phi, seed)
-        sd = torch.as_tensor(solid).cuda()
-        fl = sd == 0
-        # operating force: the benchmark's mean interstitial velocity 0.01 (Stokes-linear
-        # rescaling of a calibration solve, which is not timed)
-        u_cold = torch.zeros((3, n, n, n), dtype=torch.float32, device="cuda")
+    solid, _ = media.random_spheres((n, n, n), R, phi, seed)
+    sd = torch.as_tensor(solid).cuda()
+    fl = sd == 0
+    u_cold = torch.zeros((3, n, n, n), dtype=torch.float32, device="cuda")
+    if force is None:
+        # Stokes-linear rescaling of a calibration solve (not timed)
         mp.lb_steady(sd, (1e-5, 0.0, 0.0), u_cold, tol=1e-7, max_steps=200_000, check_every=100)
         force = (1e-5 * WORKLOAD["mean_u"] / float(u_cold[0][fl].double().mean()), 0.0, 0.0)
         u_cold.zero_()
-        torch.cuda.synchronize()
-        t0 = time.perf_counter()
-        n_cold, _, c_cold = mp.lb_steady(sd, force, u_cold, tol=1e-7, max_steps=200_000, check_every=check)
-        torch.cuda.synchronize()
-        t_cold = time.perf_counter() - t0
-        t0 = time.perf_counter()
-        u0, rho0 = surrogate.warm_start(solid, force, model)
-        torch.cuda.synchronize()
-        t_inf = time.perf_counter() - t0
-        u_warm = torch.zeros_like(u_cold)
-        n_warm, _, c_warm = mp.lb_steady(sd, force, u_warm, tol=1e-7, max_steps=200_000, check_every=check,
-                                         u_init=u0, rho_init=rho0)
-        torch.cuda.synchronize()
-        t_warm = time.perf_counter() - t0
-        rec = {"case": label, "n": n, "radius": R, "porosity": round(phi, 4), "seed": seed, "force_x": force[0],
-               "check_every": check, "cold_steps": int(n_cold), "warm_steps": int(n_warm),
-               "converged": bool(c_cold and c_warm),
-               "cold_s": round(t_cold, 4), "warm_s": round(t_warm, 4), "inference_s": round(t_inf, 4),
-               "estimate_rel_l2": float((u0 - u_cold).norm() / u_cold.norm()),
-               "flow_max_rel_diff": float((u_warm - u_cold).abs().max() / u_cold.abs().max())}
-        if label.startswith("benchmark"):
-            # the downstream observable: D(t) of the benchmark's tracer on either flow
-            Ds = []
-            for u in (u_cold, u_warm):
-                ctx = mp.mp_init(sd, u, WORKLOAD["D_b"], WORKLOAD["k_a"], WORKLOAD["k_d"], capacity=2002,
-                                 allow_negative=True)
-                mp.mp_step(ctx, 2000)
-                Ds.append(mp.mp_vacf(ctx, 0, 0)[1])
-                ctx.close()
-            rec["D_max_rel_diff"] = float(np.max(np.abs(Ds[1] / Ds[0] - 1.0)))
-        out.append(rec)
-        print(json.dumps(rec), flush=True)
-        del u_cold, u_warm, u0, rho0, sd
-    # tensor throughput of the network's forward pass on a 128^3 box (all convolutions are
-    # 3x3x3: 2 * 27 * Cin * Cout FLOPs per voxel and layer)
-    n = 128
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    n_cold, _, c_cold = mp.lb_steady(sd, force, u_cold, tol=1e-7, max_steps=200_000, check_every=check)
+    torch.cuda.synchronize()
+    t_cold = time.perf_counter() - t0
+    t0 = time.perf_counter()
+    u0, rho0 = surrogate.warm_start(solid, force, model)
+    torch.cuda.synchronize()
+    t_inf = time.perf_counter() - t0
+    u_warm = torch.zeros_like(u_cold)
+    n_warm, _, c_warm = mp.lb_steady(sd, force, u_warm, tol=1e-7, max_steps=200_000, check_every=check,
+                                     u_init=u0, rho_init=rho0)
+    torch.cuda.synchronize()
+    t_warm = time.perf_counter() - t0
+    rec = {"case": label, "n": n, "radius": R, "porosity": round(phi, 4), "seed": seed, "force_x": force[0],
+           "check_every": check, "cold_steps": int(n_cold), "warm_steps": int(n_warm),
+           "converged": bool(c_cold and c_warm),
+           "cold_s": round(t_cold, 4), "warm_s": round(t_warm, 4), "inference_s": round(t_inf, 4),
+           "estimate_rel_l2": float((u0 - u_cold).norm() / u_cold.norm()),
+           "flow_max_rel_diff": float((u_warm - u_cold).abs().max() / u_cold.abs().max())}
+    if d_steps > 0:
+        # the downstream observable: D(t) of the benchmark's tracer on either flow
+        Ds = []
+        for u in (u_cold, u_warm):
+            ctx = mp.mp_init(sd, u, WORKLOAD["D_b"], WORKLOAD["k_a"], WORKLOAD["k_d"], capacity=d_steps + 2,
+                             allow_negative=True)
+            mp.mp_step(ctx, d_steps)
+            Ds.append(mp.mp_vacf(ctx, 0, 0)[1])
+            ctx.close()
+        rec["D_steps"] = d_steps
+        rec["D_max_rel_diff"] = float(np.max(np.abs(Ds[1] / Ds[0] - 1.0)))
+    return rec
+
+
+def forward_roofline(surrogate, model, n=128):
+    """Tensor throughput of the network's forward pass on an n^3 box (all convolutions are
+    3x3x3: 2 * 27 * Cin * Cout FLOPs per voxel and layer), CUDA events over five passes."""
+    import torch
     x0 = torch.zeros((1, n ** 3, 16), dtype=torch.bfloat16, device="cuda")
     levels = {"e0a": 0, "e0b": 0, "e1a": 1, "e1b": 1, "e2a": 2, "e2b": 2, "b0": 3, "b1": 3, "d2a": 2, "d2b": 2,
               "d1a": 1, "d1b": 1, "d0a": 0, "d0b": 0, "out": 0}
@@ -465,10 +456,48 @@ def run_surrogate(args):
     pp = os.path.join(ROOT, "MEASURED_PEAKS.json")
     if os.path.exists(pp):
         peak = json.load(open(pp)).get("bf16_tflops")
-    tensor = {"kernel": "sg_conv3d forward pass, 128^3 box", "bound": "tensor", "achieved": flops / fwd_s / 1e12,
-              "peak": peak, "unit": "TFLOP/s", "frac": (flops / fwd_s / 1e12 / peak) if peak else None,
-              "flops": flops, "ms": fwd_s * 1e3,
-              "peak_source": "measured (MEASURED_PEAKS.json bf16_tflops, burst)" if peak else "unavailable"}
+    return {"kernel": f"k_conv_tc (forward pass, {n}^3 box)", "bound": "tensor", "achieved": flops / fwd_s / 1e12,
+            "peak": peak, "unit": "TFLOP/s", "frac": (flops / fwd_s / 1e12 / peak) if peak else None,
+            "flops": flops, "ms": fwd_s * 1e3,
+            "peak_source": "measured (MEASURED_PEAKS.json bf16_tflops, burst)" if peak else "unavailable"}
+
+
+def run_warm_start_record(mp, force_x):
+    """The default line's record of the learned warm start: an unseen 256^3 medium (spheres
+    R = 6, porosity 0.40, seed 90101) from rest and from the warm start at the benchmark's
+    force, with D(t) over 1000 MP steps on either flow, and the forward pass's tensor
+    throughput on a 128^3 box."""
+    from paper_1303_2470_gb300 import media, surrogate
+    model, meta = surrogate.load()
+    rec = warm_start_case(mp, surrogate, model, media, "unseen 256^3", 256, 6, 0.40, 90_101,
+                          force=(force_x, 0.0, 0.0), d_steps=1000)
+    return {"steps_factor": rec["cold_steps"] / rec["warm_steps"], "time_factor": rec["cold_s"] / rec["warm_s"],
+            "case": rec, "tensor_roofline": forward_roofline(surrogate, model),
+            "model": {"n_params": meta["n_params"], "train_media": meta["n_train"], "size": meta["size"]}}
+
+
+def run_surrogate(args):
+    """LB warm start from the trained surrogate against the cold start (both to residual
+    1e-7, checked every 10 steps, at the force giving the benchmark's mean interstitial
+    velocity 0.01): unseen 64^3 media, the benchmark's 128^3 medium and unseen 256^3 media. Reports steps and wall time (the warm time includes the network's inference),
+    the estimate's error, the distance between the two converged flows and, on the benchmark
+    medium, the largest relative difference of D(t) over 2000 MP steps run on either flow."""
+    import torch
+    from paper_1303_2470_gb300 import build, media
+    build.build()
+    from paper_1303_2470_gb300 import mp, surrogate
+    model, meta = surrogate.load()
+    rng = np.random.default_rng(77)
+    cases = [("unseen 64^3", 64, int(rng.integers(4, 9)), float(rng.uniform(0.3, 0.6)), 90_001 + i) for i in range(8)]
+    cases += [("benchmark medium 128^3", 128, WORKLOAD["radius"], WORKLOAD["porosity"], WORKLOAD["seed"])]
+    cases += [("unseen 256^3", 256, 6, 0.40, 90_101), ("unseen 256^3", 256, 5, 0.50, 90_102)]
+    out = []
+    for label, n, R, phi, seed in cases:
+        rec = warm_start_case(mp, surrogate, model, media, label, n, R, phi, seed,
+                              d_steps=2000 if label.startswith("benchmark") else 0)
+        out.append(rec)
+        print(json.dumps(rec), flush=True)
+    tensor = forward_roofline(surrogate, model)
     line = {"metric": "LB steps to residual 1e-7: cold start / surrogate warm start", "unit": "ratio",
             "steps_factor": {c: float(np.mean([r["cold_steps"] / r["warm_steps"] for r in out if r["case"] == c]))
                              for c in dict.fromkeys(r["case"] for r in out)},
@@ -582,6 +611,8 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-warm-start", action="store_true",
+                    help="leave out the learned warm start's record (an unseen 256^3 medium) of the default line")
     ap.add_argument("--no-probe", action="store_true",
                     help="skip the 384^3 x 4-species probe of the step beyond L2 (roofline_hbm)")
     ap.add_argument("--mp-steps", type=int, default=WORKLOAD["mp_steps"])
@@ -785,6 +816,8 @@ def main():
     }
     if rank == 0 and not args.no_probe:
         line["roofline_hbm"] = run_hbm_probe(mp, peak, peak_kind, scheme_options(args))
+    if rank == 0 and not args.no_warm_start:
+        line["warm_start"] = run_warm_start_record(mp, Fx)
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         line["cpu_baseline"] = oracle_sample(solid, int(round(lb_steps_mean)))
         line["cpu_baseline"].pop("job_s_estimate", None)

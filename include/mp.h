@@ -33,7 +33,7 @@ extern "C" {
 #define MP_ENOMEM (-2)        /* a device or host allocation failed                       */
 #define MP_ECUDA (-3)         /* a CUDA runtime call or kernel launch failed              */
 #define MP_ENEGPROB (-4)      /* a link probability or a stay fraction is negative        */
-#define MP_ENOTCONVERGED (-5) /* lb_steady reached max_steps above its tolerance          */
+#define MP_ENOTCONVERGED (-5) /* lb_steady: max_steps reached above tol, or unstable      */
 #define MP_ETIMEOUT (-6)      /* a bounded device-side wait gave up                       */
 
 /* ---- memory location of a caller pointer --------------------------------------------- */
@@ -373,8 +373,9 @@ const char* mp_last_error(void);
  *  steps_out, residual_out   host (either may be NULL): steps taken, last residual.
  *  stream        cudaStream_t or NULL. Allocates its working populations stream-ordered
  *                and frees them before returning; synchronises the stream.
- * Returns MP_OK when converged, MP_ENOTCONVERGED when max_steps ran out (u_out, steps_out
- * and residual_out are still written), MP_EINVAL, MP_ENOMEM or MP_ECUDA.
+ * Returns MP_OK when converged, MP_ENOTCONVERGED when max_steps ran out or the velocity
+ * became non-finite (an unstable run stops at that check with residual_out = +inf; u_out,
+ * steps_out and residual_out are still written), MP_EINVAL, MP_ENOMEM or MP_ECUDA.
  */
 int lb_steady(const mp_geometry* g, const double force[3], double tau, double tol,
               int64_t max_steps, int64_t check_every, const float* u_init, const float* rho_init,

@@ -142,6 +142,8 @@ __global__ void __launch_bounds__(kLbThreads, MP_LB_MIN_BLOCKS)
             if (rho_out) rho_out[n] = rho;
             res = fmax(fabs((double)ux - (double)u_prev[k]),
                        fmax(fabs((double)uy - (double)u_prev[NF + k]), fabs((double)uz - (double)u_prev[2 * NF + k])));
+            // a non-finite velocity (fmax drops NaN) counts as an infinite residual
+            if (!(fabs((double)ux) + fabs((double)uy) + fabs((double)uz) <= 1.0e300)) res = INFINITY;
             // this node's u(t) is the reference of the next check when it is due next step
             u_prev[k] = ux;
             u_prev[NF + k] = uy;
@@ -313,6 +315,7 @@ extern "C" int lb_steady(const mp_geometry* geom, const double force[3], double 
                 converged = true;
                 break;
             }
+            if (std::isinf(res)) break;  // the flow is no longer finite: give up
             // the mean of the last two iterates (g0 = t, g1 = t-1): same fixed point, and the
             // undamped period-2 modes that bounce-back sustains at confined nodes vanish
             if (t < max_steps) {
@@ -330,7 +333,10 @@ extern "C" int lb_steady(const mp_geometry* geom, const double force[3], double 
     if (steps_out) *steps_out = t;
     if (residual_out) *residual_out = res;
     if (!converged) {
-        set_error("lb_steady: residual " + std::to_string(res) + " above tol after " + std::to_string(t) + " steps");
+        set_error(std::isinf(res) ? "lb_steady: the velocity became non-finite by step " + std::to_string(t) +
+                                        " (unstable: tau, force or initial state)"
+                                  : "lb_steady: residual " + std::to_string(res) + " above tol after " +
+                                        std::to_string(t) + " steps");
         return MP_ENOTCONVERGED;
     }
     return MP_OK;

@@ -143,6 +143,27 @@ def test_not_converged_status_and_warm_start(mp):
     assert cold[2] and warm[2] and warm[0] < cold[0]
 
 
+def test_non_finite_flow_is_not_converged(mp):
+    """A start whose density is zero on the fluid blows the velocity up within a few steps
+    (the FP32 sum of the populations leaves a density of order 1e-8): the run stops at the
+    first check after the velocity is non-finite, long before max_steps, and reports
+    MP_ENOTCONVERGED with an infinite residual (a NaN velocity must not pass the residual
+    test)."""
+    solid, _ = media.random_spheres((16, 16, 16), 3, 0.5, seed=2)
+    u = _u_dev(solid.shape)
+    rho0 = torch.zeros(solid.shape, dtype=torch.float32, device="cuda")
+    steps, res, conv = mp.lb_steady(solid, (1e-5, 0, 0), u, tol=1e-7, max_steps=5000, check_every=10,
+                                    rho_init=rho0)
+    assert not conv and steps <= 200 and steps % 10 == 0 and np.isinf(res)
+    with pytest.raises(mp.MPError) as e:
+        mp.lb_steady(solid, (1e-5, 0, 0), u, tol=1e-7, max_steps=5000, check_every=10, rho_init=rho0,
+                     raise_on_unconverged=True)
+    assert e.value.code == mp.MP_ENOTCONVERGED and "non-finite" in str(e.value)
+    # the library stays usable: a plain solve of the same medium converges
+    steps, res, conv = mp.lb_steady(solid, (1e-5, 0, 0), u, tol=1e-7, max_steps=100_000, check_every=10)
+    assert conv and np.isfinite(res)
+
+
 @pytest.mark.parametrize("ka,kd", [(0.0, 0.0), (1e-3, 1e-2), (1e-2, 1e-3)])
 def test_poiseuille_sorption_pipeline(mp, ka, kd):
     """Slit Poiseuille flow with sorption: 16x16 periodic, H = 32, BGK tau = 1 to 1e-7, MP with
