@@ -312,20 +312,28 @@ def make_dataset(n, size, seed0, radii=(4, 8), porosity=(0.3, 0.6), log=print):
     return xs, us, rhos, info
 
 
-def train(out, n_train=512, size=64, batch=4, iters=3000, lr=1e-3, seed=1000, n_val=16, val_seed=90_000, log=print):
+def train(out, n_train=512, size=64, batch=4, iters=3000, lr=1e-3, seed=1000, n_val=16, val_seed=90_000, log=print,
+          init=None):
+    """Generates the dataset and trains; `init`: a weights file to start from (fine-tuning:
+    its output scales are kept, so that its targets keep their meaning)."""
     torch = _torch()
     from . import mp
     xs, us, rhos, info = make_dataset(n_train, size, seed, log=log)
     xv, uv, rv, _ = make_dataset(n_val, size, val_seed, log=log)      # held-out media
-    # output scales: RMS of u/F and of (rho - 1)/F over the forced fluid (targets O(1))
-    su, sr, cnt = 0.0, 0.0, 0
-    for x0, u, r in zip(xs, us, rhos):
-        m = x0[:, 1].float().view(size, size, size) > 0.5
-        su += float((u.pow(2).sum(0)[m]).sum()) / F_TRAIN ** 2
-        sr += float(((r - 1.0).pow(2)[m]).sum()) / F_TRAIN ** 2
-        cnt += int(m.sum())
-    s_u = float(np.sqrt(su / (3 * cnt)))
-    s_rho = float(np.sqrt(sr / cnt))
+    meta0 = None
+    if init is not None:
+        model, meta0 = load(init)
+        s_u, s_rho = model.s_u, model.s_rho
+    else:
+        # output scales: RMS of u/F and of (rho - 1)/F over the forced fluid (targets O(1))
+        su, sr, cnt = 0.0, 0.0, 0
+        for x0, u, r in zip(xs, us, rhos):
+            m = x0[:, 1].float().view(size, size, size) > 0.5
+            su += float((u.pow(2).sum(0)[m]).sum()) / F_TRAIN ** 2
+            sr += float(((r - 1.0).pow(2)[m]).sum()) / F_TRAIN ** 2
+            cnt += int(m.sum())
+        s_u = float(np.sqrt(su / (3 * cnt)))
+        s_rho = float(np.sqrt(sr / cnt))
 
     def targets(flows, dens):
         out = []
@@ -336,7 +344,8 @@ def train(out, n_train=512, size=64, batch=4, iters=3000, lr=1e-3, seed=1000, n_
         return out
     ts, tv = targets(us, rhos), targets(uv, rv)
     del us, uv, rhos, rv
-    model = Surrogate(seed=seed)
+    if init is None:
+        model = Surrogate(seed=seed, s_u=s_u, s_rho=s_rho)
     rng = np.random.default_rng(seed + 1)
     V = size ** 3
     loss = torch.zeros(1, dtype=torch.float64, device="cuda")
@@ -377,6 +386,10 @@ def train(out, n_train=512, size=64, batch=4, iters=3000, lr=1e-3, seed=1000, n_
             "loss_history": hist, "val_history": vhist, "n_val": n_val, "val_seed": val_seed,
             "train_seconds": time.time() - t0, "n_params": model.n_params(),
             "dataset_lb_steps_mean": float(np.mean([d["lb_steps"] for d in info]))}
+    if meta0 is not None:
+        # the runs this one continues, oldest first
+        meta["previous"] = meta0.get("previous", []) + [{k: v for k, v in meta0.items()
+                                                          if k not in ("loss_history", "val_history", "previous")}]
     np.savez(out, meta=json.dumps(meta), **model.state())
     return model, meta
 
@@ -392,12 +405,13 @@ def main():
     tr.add_argument("--iters", type=int, default=3000)
     tr.add_argument("--lr", type=float, default=1e-3)
     tr.add_argument("--seed", type=int, default=1000)
+    tr.add_argument("--init", default=None, help="weights file to fine-tune from (keeps its output scales)")
     args = ap.parse_args()
     from . import build
     build.build()
     if args.cmd == "train":
         _, meta = train(args.out, args.n_train, args.size, args.batch, args.iters, args.lr, args.seed,
-                        log=lambda s: print(s, flush=True))
+                        log=lambda s: print(s, flush=True), init=args.init)
         print(json.dumps({k: v for k, v in meta.items() if k not in ("loss_history", "val_history")}))
         print("held-out loss", meta["val_history"])
 
