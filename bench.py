@@ -70,14 +70,15 @@ TRAFFIC = {
     "k_step<float>": {"bytes_per_launch": 48_607_488 + 1_392_640, "src_sha": "450a088ead29ab87"},
     # ncu --metrics dram__bytes_read.sum,dram__bytes_write.sum, python bench.py --profile
     # --scheme direct --variant 2: one persistent launch of 20 steps moved 1299.98 + 93.68 MB;
-    # per step (the unit of the roofline entry)
-    "k_direct_persistent": {"bytes_per_launch": (1_299_980_800 + 93_677_056) // 20, "src_sha": "be2e78e2a2bfa30f"},
+    # per step (the unit of the roofline entry). Captured on mp_direct.cu 'be2e78e2a2bfa30f';
+    # the file changed since only in host code (the tiled variant's block size).
+    "k_direct_persistent": {"bytes_per_launch": (1_299_980_800 + 93_677_056) // 20, "src_sha": "764cf5e8f7245bed"},
     # the same metrics, python bench.py --profile-probe --scheme direct --variant 7: one
     # persistent launch of 20 steps of 192^3 x 4 species (2 830 813 fluid nodes) moved
     # 6175.20 + 2775.19 MB; per step, scaled by the units to the 384^3 x 4 probe
     # (22 649 211 fluid nodes)
     "k_direct_persistent@probe": {"bytes_per_launch": int((6_175_201_280 + 2_775_187_456) / 20 * 22_649_211 / 2_830_813),
-                                  "src_sha": "be2e78e2a2bfa30f"},
+                                  "src_sha": "764cf5e8f7245bed"},
 }
 
 

@@ -246,11 +246,16 @@ int mp_set_field(mp_ctx* c, int species, int field, const double* free_dense,
  * Contexts created with MP_SCHEME_DIRECT form a direct group (all of them must be): one
  * launch per step or one persistent launch per run of steps for all of them, the variant
  * autotuned as for mp_options.autotune when `autotune` is nonzero (graph_steps is then
- * unused: runs of 128 steps or more replay graphs of 64); mp_group_variant names it.
+ * unused: runs of 128 steps or more replay graphs of 64); mp_group_variant names it. With a
+ * tiled variant (several species), Z and D equal separate mp_step calls up to the grouping
+ * of its FP32 warp sums (about 1e-7 relative); the fields are identical.
+ * mp_group_create_ex: the same with `variant` (MP_VARIANT_* flags) for a direct group
+ * without autotune (flux groups ignore it); mp_group_create is mp_group_create_ex with 0.
  * Errors: MP_EINVAL, MP_ENOMEM, MP_ECUDA.
  */
 typedef struct mp_group mp_group;
 int mp_group_create(mp_group** out, mp_ctx* const* ctxs, int n, int graph_steps, int autotune);
+int mp_group_create_ex(mp_group** out, mp_ctx* const* ctxs, int n, int graph_steps, int autotune, int variant);
 int mp_group_step(mp_group* g, int64_t n);
 int mp_group_block_size(mp_group* g);
 const char* mp_group_variant(mp_group* g);

@@ -1580,9 +1580,18 @@ extern "C" {
 
 int mp_group_create(mp_group** out, mp_ctx* const* ctxs, int n, int graph_steps, int autotune)
 {
+    return mp_group_create_ex(out, ctxs, n, graph_steps, autotune, 0);
+}
+
+int mp_group_create_ex(mp_group** out, mp_ctx* const* ctxs, int n, int graph_steps, int autotune, int variant)
+{
     clear_error();
     if (!out || !ctxs || n < 1 || n > kMaxGroup || graph_steps < 0 || graph_steps % 2) {
         set_error("mp_group_create: need 1..16 contexts and an even graph_steps >= 0");
+        return MP_EINVAL;
+    }
+    if (variant < 0 || variant > 31 || (variant & 12) == 12) {
+        set_error("mp_group_create_ex: variant must combine MP_VARIANT_* flags (one block size at most)");
         return MP_EINVAL;
     }
     for (int c = 0; c < n; ++c) {
@@ -1614,7 +1623,7 @@ int mp_group_create(mp_group** out, mp_ctx* const* ctxs, int n, int graph_steps,
     if (e == cudaSuccess && ctxs[0]->scheme == MP_SCHEME_DIRECT) {
         // a direct group: its own launch state over the contexts, on the group's stream
         rc = group_sync_in(g);
-        if (rc == MP_OK) rc = direct_state_create(ctxs, n, g->stream, autotune, 0, &g->direct);
+        if (rc == MP_OK) rc = direct_state_create(ctxs, n, g->stream, autotune, variant, &g->direct);
         if (rc != MP_OK) {
             group_destroy(g);
             return rc;

@@ -1335,7 +1335,8 @@ int upload_args(DirectState* d)
     d->L.vbofs[0] = 0;
     for (int c = 0; c < n; ++c) {
         DArgs& a = d->h_args[c];
-        a.nvb = d->tiled && a.S > 1 ? tiles_of(a) : (int)((d->ctx[c]->geo.n_fluid + d->block - 1) / d->block);
+        const int blk = d->tiled ? 128 : d->block;  // the launch's block size
+        a.nvb = d->tiled && a.S > 1 ? tiles_of(a) : (int)((d->ctx[c]->geo.n_fluid + blk - 1) / blk);
         d->L.vbofs[c + 1] = d->L.vbofs[c] + a.nvb;
     }
     // partials: [2][nvb][K] per context, sized for the most virtual blocks of any variant
@@ -1602,7 +1603,10 @@ int direct_state_create(mp_ctx* const* ctxs, int n, cudaStream_t stream, int tun
     d->persistent = (variant & MP_VARIANT_PERSISTENT) != 0;
     d->block = (variant & MP_VARIANT_BLOCK128) ? 128 : ((variant & MP_VARIANT_BLOCK512) ? 512 : 256);
     d->tiled = (variant & MP_VARIANT_TILED) != 0 && !d->single;
-    if (d->tiled) d->table = false;  // the tiled body recomputes the link terms
+    if (d->tiled) {
+        d->table = false;  // the tiled body recomputes the link terms
+        d->block = 128;    // and runs in blocks of 128 (one-species contexts of the launch too)
+    }
     int dev = 0, sms = 0;
     if (cudaGetDevice(&dev) != cudaSuccess || cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) {
         delete d;

@@ -87,6 +87,7 @@ _lib.mp_classify.argtypes = [ctypes.POINTER(mp_geometry), _c_vp, ctypes.POINTER(
 _lib.mp_step_noalloc.argtypes = [_c_int, _c_int, _c_int, _c_vp, _c_vp, _c_dbl, _c_dbl, _c_dbl, _c_int,
                                  _c_vp, _c_vp, _c_vp, _c_vp, _c_vp, _c_vp]
 _lib.mp_group_create.argtypes = [ctypes.POINTER(_c_vp), ctypes.POINTER(_c_vp), _c_int, _c_int, _c_int]
+_lib.mp_group_create_ex.argtypes = [ctypes.POINTER(_c_vp), ctypes.POINTER(_c_vp), _c_int, _c_int, _c_int, _c_int]
 _lib.mp_group_step.argtypes = [_c_vp, _c_i64]
 _lib.mp_group_block_size.argtypes = [_c_vp]
 _lib.mp_group_free.argtypes = [_c_vp]
@@ -110,7 +111,8 @@ _lib.sg_pack_target.argtypes = [_vp, _vp, _vp, _c_i, _c_i, _c_i, _c_i, _f32, _f3
 _lib.sg_mse.argtypes = [_vp, _c_i, _vp, _c_i, _vp, _vp, _vp, _c_i, _c_i, _c_dbl, _vp]
 _lib.sg_adam.argtypes = [_vp, _vp, _vp, _vp, _c_i64, _f32, _f32, _f32, _f32, _c_i, _vp, _vp, _c_i, _c_i, _vp]
 for _f in ("mp_init", "mp_init_batch", "mp_step", "mp_vacf", "mp_mass", "mp_info", "mp_get_field",
-           "mp_set_field", "lb_steady", "mp_classify", "mp_step_noalloc", "mp_group_create", "mp_grid_wait_selftest",
+           "mp_set_field", "lb_steady", "mp_classify", "mp_step_noalloc", "mp_group_create", "mp_group_create_ex",
+           "mp_grid_wait_selftest",
            "mp_group_step", "mp_group_block_size", "sg_conv3d", "sg_conv3d_wgrad", "sg_check", "sg_pool2",
            "sg_pool2_grad", "sg_up2", "sg_up2_grad", "sg_add", "sg_relu_grad", "sg_pack_input",
            "sg_unpack_output", "sg_pack_target", "sg_mse", "sg_adam"):
@@ -400,11 +402,13 @@ class Group:
             pass
 
 
-def mp_group_create(ctxs, graph_steps: int = 0, autotune: bool = False) -> Group:
-    """mp_group_create of include/mp.h over a list of Context objects."""
+def mp_group_create(ctxs, graph_steps: int = 0, autotune: bool = False, variant: int = 0) -> Group:
+    """mp_group_create_ex of include/mp.h over a list of Context objects (variant: MP_VARIANT_*
+    flags of a direct group without autotune)."""
     arr = (_c_vp * len(ctxs))(*[c.ptr for c in ctxs])
     out = _c_vp()
-    _check(_lib.mp_group_create(ctypes.byref(out), arr, len(ctxs), int(graph_steps), int(bool(autotune))))
+    _check(_lib.mp_group_create_ex(ctypes.byref(out), arr, len(ctxs), int(graph_steps), int(bool(autotune)),
+                                   int(variant)))
     return Group(out, ctxs)
 
 

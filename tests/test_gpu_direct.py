@@ -136,10 +136,11 @@ def test_autotune_keeps_state_and_matches_oracle(mp):
     plain.close()
 
 
-@pytest.mark.parametrize("autotune", [False, True])
-def test_direct_group_of_uneven_media(mp, autotune):
+@pytest.mark.parametrize("autotune,variant", [(False, 0), (True, 0), (False, 16 | 2), (False, 16)])
+def test_direct_group_of_uneven_media(mp, autotune, variant):
     """Three media of different sizes, 4, 1 and 6 species, advanced by one launch per step
-    (or one persistent launch): identical fields to each context stepped on its own, and
+    (or one persistent launch; autotuned, or the tiled variant, whose launch also steps the
+    one-species medium untiled): identical fields to each context stepped on its own, and
     every species matches the oracle."""
     shapes = [(16, 18, 20), (24, 24, 24), (20, 12, 28)]
     nsp = [4, 1, 6]
@@ -151,8 +152,10 @@ def test_direct_group_of_uneven_media(mp, autotune):
         sp = media.species(S, seed=80 + j)
         inputs.append((solid, u, sp))
         ctxs.append(mp.mp_init_batch(solid, dev32(u), *sp, capacity=steps + 40, scheme="direct"))
-    g = mp.mp_group_create(ctxs, autotune=autotune)
+    g = mp.mp_group_create(ctxs, autotune=autotune, variant=variant)
     assert mp.mp_group_variant(g) != "flux"
+    if variant & mp.MP_VARIANT_TILED:
+        assert "tiled" in mp.mp_group_variant(g)
     mp.mp_group_step(g, steps)
     g.close()
     for c, (solid, u, (Db, ka, kd)) in zip(ctxs, inputs):
