@@ -143,18 +143,23 @@ __global__ void __launch_bounds__(kTThreads) k_conv_tc(const ConvArgs a)
     const int b = blockIdx.z;
     const int v = blockIdx.x * kTM + tid;  // this thread's result row
     // A pieces of this thread: piece p = tid + 128 i covers row p / 8, chunk p % 8 (the
-    // chunk is the same for every i); their voxel coordinates
+    // chunk is the same for every i)
     const int pj = tid & 7;
-    int px[kTPieces], py[kTPieces], pz[kTPieces];
-#pragma unroll
-    for (int i = 0; i < kTPieces; ++i) {
-        const int vr = blockIdx.x * kTM + (tid + kTThreads * i) / 8;
-        px[i] = -1;
-        py[i] = pz[i] = 0;
-        if (vr < a.V) {
-            px[i] = vr % a.W;
-            py[i] = (vr / a.W) % a.H;
-            pz[i] = vr / (a.W * a.H);
+    // source voxel of every (tap, row) of the block, periodic (-1: the row lies beyond the
+    // volume), computed once: thread t fills row t
+    __shared__ int s_src[27][kTM];
+    {
+        int x = 0, y = 0, z = 0;
+        if (v < a.V) {
+            x = v % a.W;
+            y = (v / a.W) % a.H;
+            z = v / (a.W * a.H);
+        }
+        for (int tap = 0; tap < 27; ++tap) {
+            const int dz = tap / 9 - 1, dy = (tap / 3) % 3 - 1, dx = tap % 3 - 1;
+            s_src[tap][tid] = v < a.V ? (wrap(z + a.sign * dz, a.D) * a.H + wrap(y + a.sign * dy, a.H)) * a.W +
+                                            wrap(x + a.sign * dx, a.W)
+                                      : -1;
         }
     }
     // stages: 64 consecutive elements of the flattened (tap, channel) reduction index (tap
@@ -193,17 +198,13 @@ __global__ void __launch_bounds__(kTThreads) k_conv_tc(const ConvArgs a)
         if (pj < kc / 8) {
             int tap, ch;
             chunk_of(st, pj, tap, ch);
-            const int dz = tap / 9 - 1, dy = (tap / 3) % 3 - 1, dx = tap % 3 - 1;
 #pragma unroll
             for (int i = 0; i < kTPieces; ++i) {
                 const int row = (tid + kTThreads * i) >> 3;
-                const bf16* src = xb;  // any valid address when the row lies outside the volume
-                if (px[i] >= 0) {
-                    const int xs = wrap(px[i] + a.sign * dx, a.W), ys = wrap(py[i] + a.sign * dy, a.H);
-                    const int zs = wrap(pz[i] + a.sign * dz, a.D);
-                    src = xb + ((size_t)(zs * a.H + ys) * a.W + xs) * K + ch;
-                }
-                cp_async16(abase + swz(row, pj), src, px[i] >= 0 ? 16u : 0u);
+                const int sv = s_src[tap][row];
+                // any valid address (zero-filled) when the row lies outside the volume
+                const bf16* src = xb + (sv >= 0 ? (size_t)sv * K + ch : 0);
+                cp_async16(abase + swz(row, pj), src, sv >= 0 ? 16u : 0u);
             }
         }
         const uint32_t bbase = smem_u32(sB + buf * BBytes);
