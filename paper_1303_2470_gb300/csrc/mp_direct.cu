@@ -340,22 +340,27 @@ __device__ __forceinline__ void vblock_multi(const DArgs& a, int vb, int in, dou
     const bool active = k < a.NF;
     const int M = a.M, K = a.K;
     const size_t NF = (size_t)a.NF, NI = (size_t)a.NI;
-    int ai = -1;
+    int ai = -1, n = 0;
     uint32_t mask = 0;
-    Nbr b{};
     int C[8];  // fluid-list index of each row centre (or of the first fluid node after it)
     bool xlo = true, xhi = true;  // x - 1 and x + 1 lie in r's row without wrapping
     const float4* o = reinterpret_cast<const float4*>(a.own) + (size_t)(active ? k : 0) * kOW4;
     if (active) {
-        const int n = ld_stream(a.flist + k);
+        n = ld_stream(a.flist + k);
         mask = ld_stream(a.fmask + k);
         ai = ld_stream(a.aidx + k);
-        b = nbrs_of(a.nx, a.ny, a.nz, a.dx, a.dxy, n);
+        const Nbr b = nbrs_of(a.nx, a.ny, a.nz, a.dx, a.dxy, n);
 #pragma unroll
         for (int j = 0; j < 8; ++j) C[j] = fluid_index(a.fw, src_of(b, row_centre(j)));
         xlo = b.oxm == -1;
         xhi = b.oxp == 1;
     }
+    // the source of link i where x - 1 or x + 1 wraps around the box (rare): the periodic
+    // neighbourhood is rebuilt from n there, so that it is not kept live through the loop
+    auto wrapped_source = [&](int i) {
+        const Nbr b = nbrs_of(a.nx, a.ny, a.nz, a.dx, a.dxy, n);
+        return fluid_index(a.fw, src_of(b, i));
+    };
     const int cpn = a.SP / kSC;
 #pragma unroll 1
     for (int pass = 0; pass < kMaxPass; ++pass) {
@@ -371,7 +376,16 @@ __device__ __forceinline__ void vblock_multi(const DArgs& a, int vb, int in, dou
 #pragma unroll
             for (int i = 1; i < kQ; ++i) {
                 if (!((mask >> (i - 1)) & 1u)) continue;
-                const int s = source_index(i, k, C, mask, xlo, xhi, b, a.fw);
+                const int row = row_of(i);
+                const int base = row < 0 ? k : C[row < 0 ? 0 : row];
+                int s;
+                if (cx(i) == 0)
+                    s = base;
+                else if (cx(i) > 0)
+                    s = xlo ? base - 1 : wrapped_source(i);
+                else
+                    s = xhi ? base + (row < 0 ? 1 : (int)((mask >> (row_centre(row < 0 ? 0 : row) - 1)) & 1u))
+                            : wrapped_source(i);
                 float q;
                 if constexpr (kTable) {
                     q = ld_stream(a.tab + tab_at(k, i));
