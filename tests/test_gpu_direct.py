@@ -219,3 +219,36 @@ def test_sharded_units_through_the_library_match_oracle(mp):
         solid, u, (Db, ka, kd) = meds[m]
         ref = oracle.run(oracle.Problem(solid, u.astype(np.float64), Db[s], ka[s], kd[s]), g=0, nsteps=60)
         assert _z_err(Z, ref.Z) < 1e-4 and _d_err(D, ref.D) < 1e-4
+
+
+def test_field_io_of_fluid_list_storage(mp):
+    """Several species in the direct scheme keep their fields over the fluid list only:
+    mp_set_field then mp_get_field returns the dense input on fluid nodes and zero on solids,
+    and a step from the set state equals the flux scheme's (dense storage) to FP32 rounding,
+    with the total mass kept."""
+    solid, _ = media.random_spheres((14, 15, 17), 2.5, 0.55, seed=21)
+    u = dev32(media.drift_flow(solid, 0.01, 0.01, seed=22))
+    Db, ka, kd = media.species(3, seed=23, D_b=(0.03, 0.1))
+    rng = np.random.default_rng(24)
+    X = rng.random(solid.shape) * (solid == 0)
+    Xa = rng.random(solid.shape) * (solid == 0)
+    ctxs = [mp.mp_init_batch(solid, u, Db, ka, kd, capacity=20, scheme=sc) for sc in ("direct", "flux")]
+    for c in ctxs:
+        mp.mp_set_field(c, 2, 0, X, Xa)
+    G, Ga = mp.mp_get_field(ctxs[0], 2, 0)
+    assert np.array_equal(G, X.astype(np.float32).astype(np.float64))
+    assert np.all(G[solid != 0] == 0)
+    ifc = Ga != 0
+    assert np.array_equal(Ga[ifc], Xa.astype(np.float32).astype(np.float64)[ifc])
+    m0 = mp.mp_mass(ctxs[0], 2)
+    for c in ctxs:
+        mp.mp_step(c, 3)
+    for f in range(2):
+        a, aa = mp.mp_get_field(ctxs[0], 2, f)
+        b, bb = mp.mp_get_field(ctxs[1], 2, f)
+        assert np.max(np.abs(a - b)) <= 1e-5 * np.abs(b).max()
+        assert np.max(np.abs(aa - bb)) <= 1e-5 * max(np.abs(bb).max(), 1e-30)
+    m1 = mp.mp_mass(ctxs[0], 2)
+    assert abs((m1[0] + m1[1]) - (m0[0] + m0[1])) <= 1e-6 * (m0[0] + m0[1])
+    for c in ctxs:
+        c.close()
