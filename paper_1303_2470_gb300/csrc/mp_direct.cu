@@ -487,14 +487,16 @@ __device__ __forceinline__ void vblock_multi(const DArgs& a, int vb, int in, dou
 // ---------------------------------------------------------------------------------------
 // Several species, tiled: a virtual block is a tile of 32 x kRows lattice columns (x, y)
 // over a segment of planes z0 .. z1 - 1 (kRows = 2 per warp). The block marches along z with
-// a ring of four planes of the tile plus a one-node halo in x and y in shared memory: per
-// position the 32-byte field chunk and the flow vector of the node (if fluid) and its
-// fluid-list index (-1 if solid), filled by asynchronous 16-byte copies through L2 two planes
-// ahead of the plane being computed. Each warp owns two rows of the tile; their fluid nodes
-// are packed onto its lanes, and every open link reads its source from shared memory. The
-// per-node arithmetic is that of vblock_multi (same link order and roundings), so the fields
-// are bitwise the same; the Z terms are summed over a warp per plane (FP32) and over the
-// planes in FP64. Several chunks of species: one march per chunk.
+// a ring of planes (three, or four with MP_TILE_SLOTS 4) of the tile plus a one-node halo in x
+// and y in shared memory: per position the 32-byte field chunk and the flow vector of the
+// node (zero if solid), its fluid-list index (-1 if solid) and its interface index, filled by
+// asynchronous 16-byte copies through L2 (three slots: the copies of plane z + 2 are issued
+// once plane z is computed; four: while it is computed). Each warp owns two rows of the tile;
+// their fluid nodes are packed onto its lanes, and every link reads its source from shared
+// memory (a closed link meets zeros and adds p * 0 = 0). The per-node arithmetic is that of
+// vblock_multi (same link order and roundings), so the fields are bitwise the same; the Z
+// terms are summed over a warp per plane (FP32) and over the planes in FP64. Several chunks
+// of species: one march per chunk.
 // ---------------------------------------------------------------------------------------
 constexpr int kTileX = 32;
 constexpr int kTilePX = kTileX + 2;
