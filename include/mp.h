@@ -77,7 +77,10 @@ extern "C" {
  * fluid node). FP32 only. Link probabilities are bitwise those of MP_SCHEME_FLUX; total mass
  * is conserved up to the FP32 rounding of each node's outgoing sum (a relative error below
  * 2^-25 of X(r) per step, of random sign across the nodes of a porous medium; in media with
- * few distinct nodes, such as slits, it adds up coherently). */
+ * few distinct nodes, such as slits, it adds up coherently). With several species the fields
+ * are stored for the fluid nodes only (in the order of the sorted fluid list; mp_get_field
+ * and mp_set_field still exchange dense arrays), which takes the porosity's share of the
+ * memory of the flux scheme's dense fields. */
 #define MP_SCHEME_DIRECT 1
 
 /* A medium: the solid mask of an nx*ny*nz periodic lattice. */
