@@ -126,6 +126,48 @@ __device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity)
     }
 }
 
+// Epilogue of the tensor-core convolutions: warp w reads accumulator rows 32w..32w+31 (its
+// lanes' voxels) from tensor memory, adds the bias, applies the ReLU and stores BF16 and/or
+// FP32 outputs of voxel v, channels n0..n0+BN-1.
+__device__ __forceinline__ void conv_epilogue(const ConvArgs& a, uint32_t tmem, int warp, int b, int v, int n0, int BN)
+{
+    const bool vok = v < a.V;
+    for (int c0 = 0; c0 < BN; c0 += 16) {
+        uint32_t r[16];
+        const uint32_t addr = tmem + ((uint32_t)(32 * warp) << 16) + (uint32_t)c0;
+        asm volatile(
+            "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
+            : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
+              "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
+            : "r"(addr));
+        asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+        if (!vok) continue;
+        const size_t o = ((size_t)b * a.V + v) * a.N + n0 + c0;
+        float f[16];
+#pragma unroll
+        for (int c = 0; c < 16; ++c) {
+            float t = __uint_as_float(r[c]) + (a.bias ? a.bias[n0 + c0 + c] : 0.0f);
+            f[c] = a.relu ? fmaxf(t, 0.0f) : t;
+        }
+        if (a.y) {
+            uint32_t h[8];
+#pragma unroll
+            for (int c = 0; c < 8; ++c) {
+                const __nv_bfloat162 p2 = __floats2bfloat162_rn(f[2 * c], f[2 * c + 1]);
+                h[c] = *reinterpret_cast<const uint32_t*>(&p2);
+            }
+            uint4* dst = reinterpret_cast<uint4*>(a.y + o);
+            dst[0] = make_uint4(h[0], h[1], h[2], h[3]);
+            dst[1] = make_uint4(h[4], h[5], h[6], h[7]);
+        }
+        if (a.yf) {
+            float4* dst = reinterpret_cast<float4*>(a.yf + o);
+#pragma unroll
+            for (int c = 0; c < 4; ++c) dst[c] = make_float4(f[4 * c], f[4 * c + 1], f[4 * c + 2], f[4 * c + 3]);
+        }
+    }
+}
+
 template <int kK>  // input channels, 0: a.K at run time
 __global__ void __launch_bounds__(kTThreads) k_conv_tc(const ConvArgs a)
 {
@@ -261,43 +303,130 @@ __global__ void __launch_bounds__(kTThreads) k_conv_tc(const ConvArgs a)
     if (ok) ok = mbar_wait(smem_u32(&mbar[(nst - 1) % kTStages]), (uint32_t)(((nst - 1) / kTStages) & 1));
     if (!ok && tid == 0) atomicExch(&g_sg_tc_fail, 1);
     asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-    if (__syncthreads_and(ok)) {
-        const bool vok = v < a.V;
-        for (int c0 = 0; c0 < BN; c0 += 16) {
-            uint32_t r[16];
-            const uint32_t addr = tmem + ((uint32_t)(32 * warp) << 16) + (uint32_t)c0;
-            asm volatile(
-                "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
-                : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
-                  "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
-                : "r"(addr));
-            asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
-            if (!vok) continue;
-            const size_t o = ((size_t)b * a.V + v) * a.N + n0 + c0;
-            float f[16];
+    if (__syncthreads_and(ok)) conv_epilogue(a, tmem, warp, b, v, n0, BN);
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+    __syncthreads();
+    if (warp == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(ncols));
+}
+
+// ---------------------------------------------------------------------------------------
+// The same convolution where a block's 128 voxels are one stretch of an x-row (W a multiple
+// of 128) and K <= 64: the three taps that differ only in dx read the same source row, so a
+// stage holds that row once — the 130 voxels x0 - 1 .. x0 + 128 (periodic) of the source
+// row (y + s dy, z + s dz), s the sign — and the taps dx = -1, 0, +1 are three groups of MMAs
+// whose A descriptors start 0, 1 or 2 rows into it (the 128-byte swizzle is keyed to the
+// absolute shared-memory address, so a descriptor may start at any row of an atom). Nine
+// stages, one per (dz, dy), in tap order; within a stage the taps in dx order and each tap's
+// channels in order, so the accumulation order is that of k_conv_tc and the outputs are
+// bitwise the same. Three B tiles (one per dx) per stage.
+// ---------------------------------------------------------------------------------------
+constexpr int kRRows = 136;                  // staged source row: 130 voxels in 17 atoms
+constexpr int kRABytes = (kRRows / 8) * kTAtom;
+constexpr int kRMaxN = 64;                   // output channels: the ring stays below 90 KB
+
+template <int kK>
+__global__ void __launch_bounds__(kTThreads) k_conv_row(const ConvArgs a)
+{
+    static_assert(kK == 16 || kK == 32 || kK == 64, "one swizzle atom row per voxel");
+    extern __shared__ __align__(1024) unsigned char tc_smem_raw[];
+    __shared__ __align__(8) uint64_t mbar[kTStages];
+    __shared__ uint32_t tmem_base;
+    const int tid = threadIdx.x, warp = tid >> 5;
+    const int n0 = blockIdx.y * kTMaxN;
+    const int BN = a.N - n0 < kTMaxN ? a.N - n0 : kTMaxN;  // a multiple of 16
+    const int BTile = (BN / 8) * kTAtom;                   // one tap's B tile
+    unsigned char* tc_smem = tc_smem_raw + ((kTAtom - (smem_u32(tc_smem_raw) & (kTAtom - 1))) & (kTAtom - 1));
+    unsigned char* sA = tc_smem;
+    unsigned char* sB = tc_smem + kTStages * kRABytes;
+    const int b = blockIdx.z;
+    const int v0 = blockIdx.x * kTM, v = v0 + tid;
+    const int x0 = v0 % a.W, y = (v0 / a.W) % a.H, z = v0 / (a.W * a.H);
+    constexpr int kJ = kK / 8;  // 16-byte chunks of a voxel's channels
+    uint32_t ncols = 32;
+    while ((int)ncols < BN) ncols <<= 1;
+    if (tid == 0) {
+        for (int s = 0; s < kTStages; ++s) asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(&mbar[s])));
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    if (warp == 0) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(&tmem_base)),
+                     "r"(ncols));
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
+    }
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+    __syncthreads();
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+    const uint32_t tmem = tmem_base;
+    const bf16* xb = a.x + (size_t)b * a.V * kK;
+
+    // stage st = 3 (dz + 1) + (dy + 1): the source row and the three taps' weights
+    auto load_stage = [&](int st, int buf) {
+        const int dz = st / 3 - 1, dy = st % 3 - 1;
+        const int ys = wrap(y + a.sign * dy, a.H), zs = wrap(z + a.sign * dz, a.D);
+        const bf16* row = xb + (size_t)(zs * a.H + ys) * a.W * kK;
+        const uint32_t abase = smem_u32(sA + buf * kRABytes);
+        for (int p = tid; p < 130 * kJ; p += kTThreads) {
+            const int r = p / kJ, j = p - r * kJ;
+            const int x = wrap(x0 - 1 + r, a.W);
+            cp_async16(abase + swz(r, j), row + (size_t)x * kK + 8 * j, 16u);
+        }
+        const uint32_t bbase = smem_u32(sB + buf * 3 * BTile);
+        for (int p = tid; p < 3 * BN * kJ; p += kTThreads) {
+            const int t = p / (BN * kJ), q = p - t * (BN * kJ);
+            const int n = q / kJ, j = q - n * kJ;
+            const int tap = 3 * st + t;  // 9 (dz + 1) + 3 (dy + 1) + (dx + 1)
+            cp_async16(bbase + t * BTile + swz(n, j), a.w + ((size_t)tap * a.N + n0 + n) * kK + 8 * j, 16u);
+        }
+    };
+
+    bool ok = true;
+    constexpr int nst = 9;
+    for (int s = 0; s < kTStages - 1; ++s) {
+        load_stage(s, s);
+        asm volatile("cp.async.commit_group;" ::: "memory");
+    }
+    for (int st = 0; st < nst; ++st) {
+        const int buf = st % kTStages;
+        const int nxt = st + kTStages - 1;
+        if (nxt < nst) {
+            if (st >= 1) ok = mbar_wait(smem_u32(&mbar[(st - 1) % kTStages]), (uint32_t)(((st - 1) / kTStages) & 1));
+            if (ok) load_stage(nxt, nxt % kTStages);
+        }
+        asm volatile("cp.async.commit_group;" ::: "memory");
+        asm volatile("cp.async.wait_group %0;" ::"n"(kTStages - 1) : "memory");
+        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+        if (__syncthreads_or(!ok)) {
+            ok = false;
+            break;
+        }
+        if (tid == 0) {
+            asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+            const uint32_t abase = smem_u32(sA + buf * kRABytes), bbase = smem_u32(sB + buf * 3 * BTile);
+            const uint32_t idesc = tc_idesc(BN);
 #pragma unroll
-            for (int c = 0; c < 16; ++c) {
-                float t = __uint_as_float(r[c]) + (a.bias ? a.bias[n0 + c0 + c] : 0.0f);
-                f[c] = a.relu ? fmaxf(t, 0.0f) : t;
-            }
-            if (a.y) {
-                uint32_t h[8];
+            for (int t = 0; t < 3; ++t) {
+                // tap dx = t - 1 reads source voxel x + s dx: row 1 + s dx of the stage
+                const uint32_t arow = (uint32_t)(1 + a.sign * (t - 1)) * 128u;
 #pragma unroll
-                for (int c = 0; c < 8; ++c) {
-                    const __nv_bfloat162 p2 = __floats2bfloat162_rn(f[2 * c], f[2 * c + 1]);
-                    h[c] = *reinterpret_cast<const uint32_t*>(&p2);
+                for (int kk = 0; kk < kK; kk += 16) {
+                    const uint64_t ad = tc_desc(abase + arow + kk * 2), bd = tc_desc(bbase + t * BTile + kk * 2);
+                    const uint32_t accum = (st > 0 || t > 0 || kk > 0) ? 1u : 0u;
+                    asm volatile(
+                        "{\n.reg .pred p;\nsetp.ne.b32 p, %4, 0;\n"
+                        "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}" ::"r"(tmem),
+                        "l"(ad), "l"(bd), "r"(idesc), "r"(accum));
                 }
-                uint4* dst = reinterpret_cast<uint4*>(a.y + o);
-                dst[0] = make_uint4(h[0], h[1], h[2], h[3]);
-                dst[1] = make_uint4(h[4], h[5], h[6], h[7]);
             }
-            if (a.yf) {
-                float4* dst = reinterpret_cast<float4*>(a.yf + o);
-#pragma unroll
-                for (int c = 0; c < 4; ++c) dst[c] = make_float4(f[4 * c], f[4 * c + 1], f[4 * c + 2], f[4 * c + 3]);
-            }
+            asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
+                             smem_u32(&mbar[buf]))
+                         : "memory");
         }
     }
+    asm volatile("cp.async.wait_all;" ::: "memory");
+    if (ok) ok = mbar_wait(smem_u32(&mbar[(nst - 1) % kTStages]), (uint32_t)(((nst - 1) / kTStages) & 1));
+    if (!ok && tid == 0) atomicExch(&g_sg_tc_fail, 1);
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+    if (__syncthreads_and(ok)) conv_epilogue(a, tmem, warp, b, v, n0, BN);
     asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
     __syncthreads();
     if (warp == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(ncols));
@@ -671,6 +800,17 @@ int sg_conv3d(const void* x, const void* w, const float* bias, void* y, float* y
     }
     ConvArgs a{(const bf16*)x, (const bf16*)w, bias, (bf16*)y, yf, D, H, W, D * H * W, K, N, sign, relu != 0};
     const int bn = N < kTMaxN ? N : kTMaxN;
+    if (W % kTM == 0 && (K == 16 || K == 32 || K == 64) && N <= kRMaxN) {
+        // blocks of 128 voxels lie in one x-row: the row-staged kernel
+        void (*rkern)(const ConvArgs) = K == 16 ? k_conv_row<16> : K == 32 ? k_conv_row<32> : k_conv_row<64>;
+        const size_t rsmem = (size_t)kTStages * (kRABytes + 3 * (size_t)(bn / 8) * kTAtom) + kTAtom;
+        MP_CUDA(cudaFuncSetAttribute(rkern, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                     (int)(kTStages * (kRABytes + 3 * (kRMaxN / 8) * kTAtom) + kTAtom)));
+        dim3 grid(a.V / kTM, (N + kTMaxN - 1) / kTMaxN, B);
+        rkern<<<grid, kTThreads, rsmem, (cudaStream_t)stream>>>(a);
+        MP_CUDA(cudaGetLastError());
+        return MP_OK;
+    }
     // the ring plus room to align it to a 1024-byte boundary
     const size_t smem = (size_t)kTStages * (kTABytes + (size_t)(bn / 8) * kTAtom) + kTAtom;
     // instances with the input-channel count fixed at compile time for the network's layers

@@ -48,7 +48,10 @@ def _ref_conv(x, w, bias, sign=1):
 @pytest.mark.parametrize("shape,K,N,relu", [((2, 4, 8, 12), 32, 48, True), ((1, 6, 5, 7), 16, 16, False),
                                             ((1, 8, 8, 8), 128, 64, True), ((2, 6, 9, 10), 64, 32, True),
                                             ((1, 5, 7, 6), 48, 32, False), ((1, 4, 6, 10), 96, 96, True),
-                                            ((1, 3, 4, 9), 80, 272, False)])
+                                            ((1, 3, 4, 9), 80, 272, False),
+                                            # x-rows of 128 and 256 voxels: the row-staged kernel
+                                            ((1, 3, 2, 128), 16, 32, True), ((2, 2, 3, 128), 32, 16, False),
+                                            ((1, 2, 2, 256), 64, 64, True), ((1, 3, 1, 128), 64, 96, False)])
 def test_conv_forward_matches_torch(mp, shape, K, N, relu):
     B, D, H, W = shape
     rng = np.random.default_rng(1)
@@ -68,8 +71,11 @@ def test_conv_forward_matches_torch(mp, shape, K, N, relu):
     assert float((y.float().cpu() - ref).abs().max()) <= 2.0 ** -8 * scale
 
 
-def test_conv_input_and_weight_gradients_match_autograd(mp):
-    B, D, H, W, K, N = 2, 4, 6, 8, 32, 48
+@pytest.mark.parametrize("B,D,H,W,K,N", [(2, 4, 6, 8, 32, 48), (1, 3, 2, 128, 32, 16)])
+def test_conv_input_and_weight_gradients_match_autograd(mp, B, D, H, W, K, N):
+    """Weight and input gradients against autograd; the second shape's input gradient (a
+    transposed convolution over x-rows of 128 voxels, 16 input channels) runs the row-staged
+    kernel."""
     rng = np.random.default_rng(2)
     x = _bf(rng.standard_normal((B, D, H, W, K)))
     wm = rng.standard_normal((27, K, N)) / np.sqrt(27 * K)          # master order [27][Cin][Cout]
