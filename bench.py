@@ -459,7 +459,8 @@ def forward_roofline(surrogate, model, n=128):
     pp = os.path.join(ROOT, "MEASURED_PEAKS.json")
     if os.path.exists(pp):
         peak = json.load(open(pp)).get("bf16_tflops")
-    return {"kernel": f"k_conv_tc (forward pass, {n}^3 box)", "bound": "tensor", "achieved": flops / fwd_s / 1e12,
+    return {"kernel": f"k_conv_row + k_conv_tc (forward pass, {n}^3 box)", "bound": "tensor",
+            "achieved": flops / fwd_s / 1e12,
             "peak": peak, "unit": "TFLOP/s", "frac": (flops / fwd_s / 1e12 / peak) if peak else None,
             "flops": flops, "ms": fwd_s * 1e3,
             "peak_source": "measured (MEASURED_PEAKS.json bf16_tflops, burst)" if peak else "unavailable"}
@@ -562,9 +563,10 @@ def run_profile_batched():
 
 
 def run_profile_surrogate():
-    """Two forward passes of the trained warm-start network on a 128^3 box (15 `k_conv_tc`
-    launches each, in layer order e0a .. out), no timing: for ncu captures of the tensor-core
-    convolution (the second pass's d0a, 64 -> 32 channels at full resolution, is launch 27)."""
+    """Two forward passes of the trained warm-start network on a 128^3 box, no timing: for ncu
+    captures of the tensor-core convolutions. Per pass, in layer order, the five layers at full
+    resolution (e0a, e0b, d0a, d0b, out) run `k_conv_row` and the ten coarser ones `k_conv_tc`;
+    the second pass's d0a (64 -> 32 channels) is `k_conv_row` launch 7."""
     import torch
     from paper_1303_2470_gb300 import build
     build.build()
