@@ -539,9 +539,10 @@ def run_profile_probe(args):
     return 0
 
 
-def run_profile_batched():
+def run_profile_batched(args):
     """Two random-sphere media (96^3, 128^3) x 16 species, 30 LB steps each, then 8 grouped
-    steps without graph or autotune: `k_step_group` launches for ncu captures."""
+    steps without graph or autotune, in the scheme and variant given: `k_step_group` (flux)
+    or `k_direct_step` / `k_direct_persistent` (direct) launches for ncu captures."""
     import torch
     from paper_1303_2470_gb300 import build, media
     build.build()
@@ -553,11 +554,14 @@ def run_profile_batched():
         u = torch.zeros((3,) + solid.shape, dtype=torch.float32, device="cuda")
         mp.lb_steady(sd, (1e-3, 0, 0), u, tol=0.0, max_steps=30, check_every=30)
         Db, ka, kd = media.species(16, seed=seed + 100)
-        ctxs.append(mp.mp_init_batch(sd, u, Db, ka, kd, capacity=16, allow_negative=True))
-    g = mp.mp_group_create(ctxs)
+        opts = scheme_options(args)
+        opts.pop("autotune", None)
+        variant = opts.pop("variant", 0)
+        ctxs.append(mp.mp_init_batch(sd, u, Db, ka, kd, capacity=16, allow_negative=True, **opts))
+    g = mp.mp_group_create(ctxs, variant=variant)
     mp.mp_group_step(g, 8)
     torch.cuda.synchronize()
-    print(json.dumps({"profile_batched": "ok", "block": mp.mp_group_block_size(g)}))
+    print(json.dumps({"profile_batched": "ok", "block": mp.mp_group_block_size(g), "variant": mp.mp_group_variant(g)}))
     g.close()
     return 0
 
@@ -650,7 +654,7 @@ def main():
     if args.profile:
         return run_profile_case(args)
     if args.profile_batched:
-        return run_profile_batched()
+        return run_profile_batched(args)
     if args.profile_probe:
         return run_profile_probe(args)
     if args.profile_surrogate:
