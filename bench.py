@@ -73,14 +73,14 @@ TRAFFIC = {
     # per step (the unit of the roofline entry). Captured on mp_direct.cu 'be2e78e2a2bfa30f';
     # the file changed since only in host code (the tiled variant's block size) and in the
     # several-species kernels (register use, comments), not in this kernel.
-    "k_direct_persistent": {"bytes_per_launch": (1_299_980_800 + 93_677_056) // 20, "src_sha": "108bf7f6f37475eb"},
+    "k_direct_persistent": {"bytes_per_launch": (1_299_980_800 + 93_677_056) // 20, "src_sha": "4588265e46e22840"},
     # the same metrics, python bench.py --profile-probe --scheme direct --variant 7: one
     # persistent launch of 20 steps of 192^3 x 4 species (2 830 813 fluid nodes) moved
     # 6175.20 + 2775.19 MB; per step, scaled by the units to the 384^3 x 4 probe
     # (22 649 211 fluid nodes). Captured on mp_direct.cu 'be2e78e2a2bfa30f'; since then the
     # kernel keeps fewer registers live (fewer spills to local memory), same data accesses.
     "k_direct_persistent@probe": {"bytes_per_launch": int((6_175_201_280 + 2_775_187_456) / 20 * 22_649_211 / 2_830_813),
-                                  "src_sha": "108bf7f6f37475eb"},
+                                  "src_sha": "4588265e46e22840"},
 }
 
 

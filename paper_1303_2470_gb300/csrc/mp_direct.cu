@@ -11,9 +11,12 @@
 // u*_g(r) = sum_i p_i(r) c_ig of the VACF sum Z_g = sum_r P_g(r) u*_g(r). A step then costs,
 // per link, one coalesced table load, one gather of the source's field record and one
 // fused multiply-add per field. The link values are bitwise those of the flux scheme
-// (mp.cu), and links into solid nodes meet zero fields (solid entries are never written), so
-// the inflow needs no open-link test. A variant recomputes q_i from the packed flow vector
-// of the source instead of reading the table (less memory traffic, more arithmetic).
+// (mp.cu). One species keeps dense fields: links into solid nodes meet zero fields (solid
+// entries are never written), so that inflow needs no open-link test. Several species keep
+// their fields for the fluid nodes only and locate each open link's source in the fluid list
+// (lattice.cuh); closed links are skipped. A variant recomputes q_i from the flow vector of
+// the source instead of reading the table (less memory traffic, more arithmetic), and for
+// several species a tiled variant stages planes of the medium in shared memory.
 //
 // Unlike the flux scheme, total mass is not conserved to the last bit: the FP32 rounding
 // of out(r) is a fixed relative error per node and step (below 2^-25 of X(r) for out < 1/2),
