@@ -74,6 +74,13 @@ TRAFFIC = {
     # the file changed since only in host code (the tiled variant's block size) and in the
     # several-species kernels (register use, comments), not in this kernel.
     "k_direct_persistent": {"bytes_per_launch": (1_299_980_800 + 93_677_056) // 20, "src_sha": "4588265e46e22840"},
+    # the same metrics, python bench.py --profile --scheme direct --variant 4 (one launch per
+    # step, link table, blocks of 128; the autotuner's choice when it times within noise of the
+    # persistent launch): three launches, 94.13 + 2.56 MB on average. ncu flushes the caches
+    # before each captured launch, so this is the cold-L2 traffic of a step (an upper bound;
+    # the persistent launch's warm steps move 69.7 MB).
+    "k_direct_step": {"bytes_per_launch": (93_998_080 + 94_247_168 + 94_153_984 + 4_150_528 + 1_185_536 + 2_335_744) // 3,
+                      "src_sha": "4588265e46e22840"},
     # the same metrics, python bench.py --profile-probe --scheme direct --variant 7: one
     # persistent launch of 20 steps of 192^3 x 4 species (2 830 813 fluid nodes) moved
     # 6175.20 + 2775.19 MB; per step, scaled by the units to the 384^3 x 4 probe
