@@ -88,6 +88,13 @@ TRAFFIC = {
     # kernel keeps fewer registers live (fewer spills to local memory), same data accesses.
     "k_direct_persistent@probe": {"bytes_per_launch": int((6_175_201_280 + 2_775_187_456) / 20 * 22_649_211 / 2_830_813),
                                   "src_sha": "4588265e46e22840"},
+    # ncu --set full, python bench.py --profile-probe --scheme direct --variant 1 (one launch per
+    # step, recomputed link terms, blocks of 256): one step of 192^3 x 4 species moved
+    # 310.77 + 128.08 MB (cold L2); scaled by the units to the 384^3 x 4 probe. Captured on
+    # mp_direct.cu 'be2e78e2a2bfa30f'; the kernel has kept fewer registers live since, same
+    # data accesses.
+    "k_direct_step@probe": {"bytes_per_launch": int((310_765_824 + 128_075_776) * 22_649_211 / 2_830_813),
+                            "src_sha": "4588265e46e22840"},
 }
 
 
